@@ -1,0 +1,167 @@
+/*
+ * eth.h -- C ABI of the GB300 enriched Taylor--Hood (Q2--Q1*) Stokes/Oseen solver.
+ *
+ * Problem (Pestana & Silvester, Sec. 2 "Stokes problem" and Sec. 3 "Oseen
+ * problem"): on a uniform n x n grid of rectangles of [x0,x1] x [y0,y1],
+ * velocity in (Q2)^2 and pressure in the two-field frame Q1 + P0
+ * (Sec. 2.1, Eq. eth_pressure_space / eth_spec), solve
+ *
+ *     [ F  B^T ] [u]   [f]        F = nu*A          (Stokes, Eq. saddle_point)
+ *     [ B  0   ] [p] = [g]        F = nu*A + N(w)   (Oseen,  Eq. oseen-system)
+ *
+ * with b(u,p) = -int p div u, Dirichlet velocity on the whole boundary, and a
+ * pressure defined only modulo span{e1, e0} (constant Q1 and constant P0
+ * pressure, Sec. 2.1 Eq. pressure_null_vector and Sec. 3 Test problem 4).
+ *
+ * Layout (all vectors FP64, device-resident unless stated otherwise):
+ *   Q2 lattice (2n+1)^2 nodes, node (i,j) at (x0 + i*hx/2, y0 + j*hy/2),
+ *   flat index j*(2n+1) + i.  Velocity u = [u_x (N_v); u_y (N_v)], N_v = (2n+1)^2.
+ *   Pressure p = [p1 ((n+1)^2 Q1 coefficients); p0 (n^2 element constants)],
+ *   element (ex,ey) has index ey*n + ex (Eq. function_basis ordering).
+ *   Full-system vectors are [u; p] of length N_t = 2 N_v + (n+1)^2 + n^2.
+ *
+ * Dirichlet treatment: the full lattice is kept; boundary velocity rows of K
+ * are identity rows and boundary velocity columns are zero elsewhere.
+ *
+ * Ownership: the caller owns every pointer argument and never hands it to the
+ * library; the handle owns its device workspace (multigrid hierarchy, Krylov
+ * basis), allocated at eth_grid_create and freed by eth_grid_destroy.
+ * Streams: all device work of a handle is enqueued on the stream given at
+ * creation.  eth_apply returns after enqueueing; eth_solve* synchronise that
+ * stream once at the end to fill eth_stats.
+ * Errors: every call returns an eth_status; no exception crosses the ABI.
+ * eth_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef ETH_H
+#define ETH_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eth_grid eth_grid;
+typedef struct eth_batch eth_batch;
+
+typedef enum {
+  ETH_OK = 0,
+  ETH_EINVAL = 1,         /* bad argument (size, pointer, option)            */
+  ETH_ENOMEM = 2,         /* device allocation failed                        */
+  ETH_ECUDA = 3,          /* CUDA runtime error                              */
+  ETH_ENOTCONV = 4,       /* tolerance not reached within maxit              */
+  ETH_EBREAKDOWN = 5,     /* Krylov breakdown (e.g. MINRES gamma^2 <= 0)     */
+  ETH_EINCONSISTENT = 6,  /* right-hand side has a null-space component      */
+  ETH_ETIMEOUT = 7,       /* bounded device wait gave up                     */
+  ETH_ENAN = 8            /* NaN or Inf in a residual                        */
+} eth_status;
+
+typedef enum { ETH_STOKES = 0, ETH_OSEEN = 1 } eth_kind;
+
+/* Operators of eth_apply.  K: full system (velocity Dirichlet rows identity);
+ * KT: its transpose (element-transposed convection); A: nu*A (Dirichlet);
+ * F: nu*A + N(w) (Dirichlet); B: [B1;B0] D_I u; BT: D_I B^T p;
+ * MQ: M_Q = [Qk R^T; R Q0] (Sec. 2.3); MV: per-component Q2 mass (no BC);
+ * K1: reduced system [F B1^T; B1 0] on [u; p1] (Sec. 3.1 Eq. reduced-system). */
+typedef enum {
+  ETH_OP_K = 0, ETH_OP_KT = 1, ETH_OP_A = 2, ETH_OP_F = 3, ETH_OP_B = 4,
+  ETH_OP_BT = 5, ETH_OP_MQ = 6, ETH_OP_MV = 7, ETH_OP_K1 = 8
+} eth_op;
+
+/* Precision of the internal arithmetic. */
+typedef enum { ETH_FP64 = 0, ETH_MIXED = 1 } eth_precision;
+
+/* Approximation of the singular pressure mass solve M_Q^+ (Sec. 2.2-2.3). */
+typedef enum { ETH_MQ_VCYCLE = 0, ETH_MQ_EXACT = 1 } eth_mq_mode;
+
+typedef struct {
+  double tol;              /* relative true residual ||b-Kx||/||b||          */
+  int maxit;               /* total Krylov iterations (all stages/passes)    */
+  int restart;             /* GMRES restart length (Oseen)                   */
+  double c_stage;          /* two-stage factor c (Sec. 3.1), Step I to c*tol */
+  int precision;           /* eth_precision                                  */
+  int mg_pre, mg_post;     /* smoothing sweeps of the velocity V-cycle       */
+  int mg_min_n;            /* coarsest grid size of the hierarchies          */
+  int mq_mode;             /* eth_mq_mode                                    */
+  int a_exact;             /* 1: exact velocity solves (inner PCG), P_1 form */
+  double inner_tol;        /* inner exact-solve tolerance when exact         */
+  double refine_inner_tol; /* mixed: relative tolerance of each inner solve  */
+  int graph;               /* 1: replay captured CUDA graphs                 */
+  int verbose;
+} eth_opts;
+
+typedef struct {
+  int iters_stage1, iters_stage2, refine_passes, iters_total;
+  double relres_true;      /* FP64 ||b - K x|| / ||b|| at exit               */
+  double relres0;          /* at entry                                       */
+  double prop2_lhs, prop2_bound; /* Sec. 3.1 Prop. 2 at the stage switch   */
+  double seconds;          /* wall time of the solve (device events)         */
+  double alg_bytes;        /* algorithmic bytes moved (estimate)             */
+  int status;              /* eth_status of the solve                        */
+  int kernel_launches;     /* device kernels launched by the solve           */
+} eth_stats;
+
+/* Sizes of an n x n grid: N_v = (2n+1)^2, N_1 = (n+1)^2, N_0 = n^2.
+ * Returns N_t = 2 N_v + N_1 + N_0, or -1 for n < 1. */
+int eth_sizes(int n, int* nv, int* n1, int* n0);
+const char* eth_status_string(eth_status s);
+const char* eth_last_error(void);
+void eth_default_opts(eth_opts* o);
+
+/* Creates a handle for an n x n grid (n >= 2, n a multiple of 2) on
+ * [x0,x1] x [y0,y1] and allocates its workspace.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  Sec. 2.1 / 3. */
+eth_status eth_grid_create(int n, double x0, double x1, double y0, double y1,
+                           eth_kind kind, void* cuda_stream, eth_grid** out);
+void eth_grid_destroy(eth_grid* g);
+
+/* Viscosity nu > 0 and, for ETH_OSEEN, the nodal Q2 wind w (device, 2*N_v
+ * FP64, Sec. 3 "discrete wind w_h"); wind_dev must be NULL for ETH_STOKES.
+ * Rebuilds the wind-dependent parts of the multigrid hierarchy. */
+eth_status eth_set_coefficients(eth_grid* g, double nu, const double* wind_dev);
+
+/* Right-hand side from the nodal Q2 body force f (device, 2*N_v FP64) and the
+ * Dirichlet data (device, 2*N_v FP64, only boundary entries read):
+ * b = [D_I (M_v f - F u_b) + D_B u_b ; -B u_b] (Sec. 2 Eq. saddle_point with
+ * Dirichlet lifting).  Requires eth_set_coefficients first. */
+eth_status eth_set_rhs(eth_grid* g, const double* f_nodal_dev, const double* ubc_dev);
+/* Copies the assembled right-hand side b (N_t FP64) into b_dev. */
+eth_status eth_get_rhs(eth_grid* g, double* b_dev);
+
+/* Solves K x = b: Stokes by MINRES (Algorithm 1) with the block-diagonal
+ * preconditioner (Eq. stokes_pre), Oseen by the two-stage PCD method
+ * (Sec. 3.1).  u_dev (2*N_v) and p_dev (N_1 + N_0) hold the initial guess on
+ * entry (boundary entries of u are overwritten by the Dirichlet data) and the
+ * solution on exit, with sum(p1) = sum(p0) = 0.  stats may be NULL. */
+eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u_dev,
+                     double* p_dev, eth_stats* stats);
+
+/* Same as eth_solve with HOST buffers: copies f_nodal and ubc (2*N_v each) in,
+ * sets the right-hand side, solves from a zero initial guess and copies u and
+ * p back.  All host<->device copies happen inside the call. */
+eth_status eth_solve_host(eth_grid* g, const eth_opts* opts, const double* f_nodal_host,
+                          const double* ubc_host, double* u_host, double* p_host,
+                          eth_stats* stats);
+
+/* Adjoint solve K^T [l_u; l_p] = [r_u; r_p] (r_p must have zero sums on the
+ * Q1 and P0 blocks).  Stokes: same solver (K symmetric).  Oseen: the two-stage
+ * solver applied to K^T = [F^T B^T; B 0] with PCD built on F1^T. */
+eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru_dev,
+                             const double* rp_dev, double* lu_dev, double* lp_dev,
+                             eth_stats* stats);
+
+/* y = op(x) for one operator (see eth_op); fp32 != 0 selects FP32 element
+ * arithmetic (inputs and outputs stay FP64).  Sizes: K, KT: N_t -> N_t;
+ * A, F, MV: 2 N_v -> 2 N_v; B: 2 N_v -> N_1+N_0; BT: N_1+N_0 -> 2 N_v;
+ * MQ: N_1+N_0 -> N_1+N_0; K1: 2 N_v+N_1 -> 2 N_v+N_1. */
+eth_status eth_apply(eth_grid* g, eth_op op, int fp32, const double* x_dev, double* y_dev);
+
+/* Batched solves of independent instances (each created with its own handle,
+ * all on the same stream). */
+eth_status eth_batch_create(int count, eth_grid* const* grids, eth_batch** out);
+eth_status eth_batch_solve(eth_batch* b, const eth_opts* opts, double* const* u_dev,
+                           double* const* p_dev, eth_stats* stats_array);
+void eth_batch_destroy(eth_batch* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ETH_H */

@@ -1,0 +1,139 @@
+// Shared definitions of the GB300 Q2--Q1* solver library (device + host).
+//
+// Quadrature: every element integral uses the 3x3 Gauss-Legendre rule on the
+// affine map of a rectangle; on the reference interval [0,1] the points are
+// 1/2 - sqrt(3/5)/2, 1/2, 1/2 + sqrt(3/5)/2 with weights 5/18, 8/18, 5/18.
+// Shape functions on [0,1]: quadratic Lagrange at {0, 1/2, 1} for velocity,
+// linear Lagrange at {0, 1} for the Q1 pressure, indicator for P0.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <string>
+#include "eth.h"
+
+namespace eth {
+
+constexpr double GOFF = 0.38729833462074168852;   // sqrt(3/5)/2
+__host__ __device__ constexpr double gq(int q) { return q == 0 ? 0.5 - GOFF : (q == 1 ? 0.5 : 0.5 + GOFF); }
+__host__ __device__ constexpr double gw(int q) { return q == 1 ? 8.0 / 18.0 : 5.0 / 18.0; }
+// quadratic Lagrange basis on [0,1] and its derivative
+__host__ __device__ constexpr double q2v(int a, double t) {
+  return a == 0 ? 2.0 * (t - 0.5) * (t - 1.0) : (a == 1 ? -4.0 * t * (t - 1.0) : 2.0 * t * (t - 0.5));
+}
+__host__ __device__ constexpr double q2d(int a, double t) {
+  return a == 0 ? 4.0 * t - 3.0 : (a == 1 ? 4.0 - 8.0 * t : 4.0 * t - 1.0);
+}
+// linear Lagrange basis on [0,1]
+__host__ __device__ constexpr double q1v(int c, double t) { return c == 0 ? 1.0 - t : t; }
+__host__ __device__ constexpr double q1d(int c) { return c == 0 ? -1.0 : 1.0; }
+
+// Table values at Gauss point q (compile-time when q, a are constants).
+#define LV(q, a) ((CT)::eth::q2v((a), ::eth::gq(q)))
+#define LD(q, a) ((CT)::eth::q2d((a), ::eth::gq(q)))
+#define NV(q, c) ((CT)::eth::q1v((c), ::eth::gq(q)))
+#define GW(q) ((CT)::eth::gw(q))
+
+// ---------------------------------------------------------------------------
+// Grid-wide deterministic reductions: every block writes one partial, the
+// last block to arrive (ticket counter) sums the partials in block order and
+// runs a scalar "finisher" on thread 0.
+// ---------------------------------------------------------------------------
+struct Scalars;
+struct Slot {
+  double* part;        // partials, >= total entries
+  unsigned* ticket;    // arrival counter (reset to 0 by the last block)
+  double* out;         // final sums
+  int total;           // number of partials expected
+  int op;              // finisher run by the last block (FIN_*)
+  Scalars* sc;         // scalar state the finisher updates
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block-wide sum of `nv` values per thread; result valid in thread 0.
+template <int NV_>
+__device__ __forceinline__ void block_sum(double (&v)[NV_]) {
+  __shared__ double sh[NV_][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < NV_; ++k) v[k] = warp_sum(v[k]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV_; ++k) sh[k][wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV_; ++k) {
+      double t = lane < nw ? sh[k][lane] : 0.0;
+      v[k] = warp_sum(t);
+    }
+  }
+}
+
+// Writes the block's NV_ partials at part[k*total + idx]; returns true on
+// thread 0 of the last block, which then holds the final sums in v.
+template <int NV_>
+__device__ __forceinline__ bool slot_arrive(const Slot& s, int idx, double (&v)[NV_]) {
+  block_sum<NV_>(v);
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV_; ++k) s.part[(size_t)k * s.total + idx] = v[k];
+    __threadfence();
+    unsigned t = atomicAdd(s.ticket, 1u);
+    last = (t == (unsigned)s.total - 1u);
+  }
+  __syncthreads();
+  if (!last) return false;
+  __threadfence();
+  // last block: sum partials in fixed order (all threads), result to thread 0
+  double acc[NV_];
+#pragma unroll
+  for (int k = 0; k < NV_; ++k) {
+    acc[k] = 0.0;
+    for (int i = threadIdx.x; i < s.total; i += blockDim.x)
+      acc[k] += ((volatile double*)s.part)[(size_t)k * s.total + i];
+  }
+  block_sum<NV_>(acc);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV_; ++k) v[k] = acc[k];
+    *s.ticket = 0u;
+  }
+  return threadIdx.x == 0;
+}
+
+}  // namespace eth
+#include "scalars.cuh"
+namespace eth {
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+void set_error(const char* fmt, ...);
+eth_status cuda_status(cudaError_t e, const char* what);
+
+#define ETH_CUDA(call)                                                   \
+  do {                                                                   \
+    cudaError_t e_ = (call);                                             \
+    if (e_ != cudaSuccess) return ::eth::cuda_status(e_, #call);         \
+  } while (0)
+
+#define ETH_TRY(call)                                                    \
+  do {                                                                   \
+    eth_status s_ = (call);                                              \
+    if (s_ != ETH_OK) return s_;                                         \
+  } while (0)
+
+inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
+
+}  // namespace eth

@@ -1,0 +1,651 @@
+// Geometric multigrid hierarchies and V-cycles (see mg.cuh).
+#include <cmath>
+#include <vector>
+#include "mg.cuh"
+
+namespace eth {
+
+// ---------------------------------------------------------------------------
+// velocity (Q2) level kernels
+// ---------------------------------------------------------------------------
+// Inverse diagonal of nu*A + N(w) at interior nodes (3x3 Gauss), 0 on the boundary.
+template <class T>
+__device__ __forceinline__ void wind_at(int N, size_t nv, int ex, int ey, const T* __restrict__ w, int qx, int qy, double& wx, double& wy) {
+  wx = 0; wy = 0;
+  for (int bb = 0; bb < 3; ++bb)
+    for (int aa = 0; aa < 3; ++aa) {
+      const double f = q2v(aa, gq(qx)) * q2v(bb, gq(qy));
+      const size_t gn = (size_t)(2 * ey + bb) * N + 2 * ex + aa;
+      wx += f * (double)w[gn];
+      wy += f * (double)w[gn + nv];
+    }
+}
+
+// streamline-diffusion parameter of an element (matches the tile kernel)
+template <class T>
+__device__ __forceinline__ double sd_delta(int N, size_t nv, int ex, int ey, const T* __restrict__ w, double h, double nu, double sdc) {
+  if (w == nullptr || sdc <= 0.0) return 0.0;
+  double wn = 0.0;
+  for (int qy = 0; qy < 3; ++qy)
+    for (int qx = 0; qx < 3; ++qx) {
+      double a, b;
+      wind_at<T>(N, nv, ex, ey, w, qx, qy, a, b);
+      wn += sqrt(a * a + b * b);
+    }
+  wn /= 9.0;
+  const double pe = wn * h / (2.0 * nu);
+  return pe > 1.0 ? sdc * h / (2.0 * wn) * (1.0 - 1.0 / pe) : 0.0;
+}
+
+template <class T>
+__global__ void k_q2_diag(int n, double hx, double hy, double nu, double sdc, const T* __restrict__ w, T* __restrict__ dinv) {
+  const int N = 2 * n + 1;
+  const size_t nv = (size_t)N * N;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N * N; node += gridDim.x * blockDim.x) {
+    const int j = node / N, i = node - j * N;
+    if (i == 0 || j == 0 || i == N - 1 || j == N - 1) { dinv[node] = 0; continue; }
+    double diag = 0.0;
+    for (int ey = (j - 2) / 2; ey <= j / 2; ++ey) {
+      const int b = j - 2 * ey;
+      if (ey < 0 || ey >= n || b < 0 || b > 2) continue;
+      for (int ex = (i - 2) / 2; ex <= i / 2; ++ex) {
+        const int a = i - 2 * ex;
+        if (ex < 0 || ex >= n || a < 0 || a > 2) continue;
+        const double dl = sd_delta<T>(N, nv, ex, ey, w, fmax(hx, hy), nu, sdc);
+        for (int qy = 0; qy < 3; ++qy)
+          for (int qx = 0; qx < 3; ++qx) {
+            const double W = gw(qx) * gw(qy) * hx * hy;
+            const double ph = q2v(a, gq(qx)) * q2v(b, gq(qy));
+            const double dx = q2d(a, gq(qx)) * q2v(b, gq(qy)) / hx;
+            const double dy = q2v(a, gq(qx)) * q2d(b, gq(qy)) / hy;
+            double wx = 0, wy = 0;
+            if (w != nullptr) wind_at<T>(N, nv, ex, ey, w, qx, qy, wx, wy);
+            const double wg = wx * dx + wy * dy;
+            diag += W * (nu * (dx * dx + dy * dy) + wg * ph + dl * wg * wg);
+          }
+      }
+    }
+    dinv[node] = (T)(1.0 / diag);
+  }
+}
+
+// x = omega D^{-1} b on the interior (first sweep from a zero guess), b copied.
+template <class TI, class T>
+__global__ void k_q2_jacobi0(int n, T omega, const T* __restrict__ dinv, const TI* __restrict__ bin, T* __restrict__ bc,
+                             T* __restrict__ x, const int* done) {
+  if (done != nullptr && *done) return;
+  const int N = 2 * n + 1;
+  const size_t nv = (size_t)N * N;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t g = k < nv ? k : k - nv;
+    const int j = (int)(g / N), i = (int)(g - (size_t)j * N);
+    const bool bnd = i == 0 || j == 0 || i == N - 1 || j == N - 1;
+    const T b = bnd ? T(0) : (T)bin[k];
+    if (bc != (const T*)bin) bc[k] = b;
+    x[k] = omega * dinv[g] * b;
+  }
+}
+
+// 1D Q2 restriction weights from coarse index I: fine offsets and weights.
+__device__ __forceinline__ int q2_rweights(int I, int* off, float* wt) {
+  if (I & 1) { off[0] = -1; wt[0] = 0.75f; off[1] = 0; wt[1] = 1.f; off[2] = 1; wt[2] = 0.75f; return 3; }
+  off[0] = -3; wt[0] = -0.125f; off[1] = -1; wt[1] = 0.375f; off[2] = 0; wt[2] = 1.f;
+  off[3] = 1; wt[3] = 0.375f; off[4] = 3; wt[4] = -0.125f;
+  return 5;
+}
+
+template <class T>
+__global__ void k_q2_restrict(int nc, const T* __restrict__ rf, T* __restrict__ bc, const int* done) {
+  if (done != nullptr && *done) return;
+  const int Nc = 2 * nc + 1, Nf = 4 * nc + 1;
+  const size_t nvc = (size_t)Nc * Nc, nvf = (size_t)Nf * Nf;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Nc * Nc; node += gridDim.x * blockDim.x) {
+    const int J = node / Nc, I = node - J * Nc;
+    if (I == 0 || J == 0 || I == Nc - 1 || J == Nc - 1) { bc[node] = 0; bc[node + nvc] = 0; continue; }
+    int ox[5], oy[5];
+    float wx[5], wy[5];
+    const int nx = q2_rweights(I, ox, wx), ny = q2_rweights(J, oy, wy);
+    T s0 = 0, s1 = 0;
+    for (int u = 0; u < ny; ++u) {
+      const size_t row = (size_t)(2 * J + oy[u]) * Nf;
+      T t0 = 0, t1 = 0;
+      for (int v = 0; v < nx; ++v) {
+        const size_t f = row + 2 * I + ox[v];
+        t0 += (T)wx[v] * rf[f];
+        t1 += (T)wx[v] * rf[f + nvf];
+      }
+      s0 += (T)wy[u] * t0;
+      s1 += (T)wy[u] * t1;
+    }
+    bc[node] = s0;
+    bc[node + nvc] = s1;
+  }
+}
+
+// 1D Q2 prolongation weights to fine index i: coarse indices and weights.
+__device__ __forceinline__ int q2_pweights(int i, int* c, float* wt) {
+  if (!(i & 1)) { c[0] = i >> 1; wt[0] = 1.f; return 1; }
+  const int E = i >> 2;
+  if ((i & 3) == 1) { c[0] = 2 * E; wt[0] = 0.375f; c[1] = 2 * E + 1; wt[1] = 0.75f; c[2] = 2 * E + 2; wt[2] = -0.125f; }
+  else { c[0] = 2 * E; wt[0] = -0.125f; c[1] = 2 * E + 1; wt[1] = 0.75f; c[2] = 2 * E + 2; wt[2] = 0.375f; }
+  return 3;
+}
+
+template <class T>
+__global__ void k_q2_prolong_add(int nc, const T* __restrict__ xc, T* __restrict__ xf, const int* done) {
+  if (done != nullptr && *done) return;
+  const int Nc = 2 * nc + 1, Nf = 4 * nc + 1;
+  const size_t nvc = (size_t)Nc * Nc, nvf = (size_t)Nf * Nf;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Nf * Nf; node += gridDim.x * blockDim.x) {
+    const int j = node / Nf, i = node - j * Nf;
+    if (i == 0 || j == 0 || i == Nf - 1 || j == Nf - 1) continue;
+    int cx[3], cy[3];
+    float wx[3], wy[3];
+    const int nx = q2_pweights(i, cx, wx), ny = q2_pweights(j, cy, wy);
+    T s0 = 0, s1 = 0;
+    for (int u = 0; u < ny; ++u)
+      for (int v = 0; v < nx; ++v) {
+        const size_t c = (size_t)cy[u] * Nc + cx[v];
+        const T f = (T)(wx[v] * wy[u]);
+        s0 += f * xc[c];
+        s1 += f * xc[c + nvc];
+      }
+    xf[node] += s0;
+    xf[node + nvf] += s1;
+  }
+}
+
+template <class T>
+__global__ void k_q2_inject(int nc, const T* __restrict__ wf, T* __restrict__ wc) {
+  const int Nc = 2 * nc + 1, Nf = 4 * nc + 1;
+  const size_t nvc = (size_t)Nc * Nc, nvf = (size_t)Nf * Nf;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Nc * Nc; node += gridDim.x * blockDim.x) {
+    const int J = node / Nc, I = node - J * Nc;
+    const size_t f = (size_t)(2 * J) * Nf + 2 * I;
+    wc[node] = wf[f];
+    wc[node + nvc] = wf[f + nvf];
+  }
+}
+
+template <class TI>
+__global__ void k_f64_from(size_t m, const TI* __restrict__ a, double* __restrict__ b) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) b[k] = (double)a[k];
+}
+template <class TO>
+__global__ void k_cast_from_f64(size_t m, const double* __restrict__ a, TO* __restrict__ b) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) b[k] = (TO)a[k];
+}
+
+// Dense matrix of the interior scalar operator on the coarsest grid (FP64 atomics, set-up only).
+__global__ void k_q2_coarse_mat(int n, double hx, double hy, double nu, double sdc, const double* __restrict__ w, double* __restrict__ D) {
+  const int N = 2 * n + 1, m = (N - 2) * (N - 2);
+  const size_t nv = (size_t)N * N;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int ey = e / n, ex = e - ey * n;
+  double wq[2][9];
+  for (int qy = 0; qy < 3; ++qy)
+    for (int qx = 0; qx < 3; ++qx) {
+      double a0 = 0, a1 = 0;
+      if (w != nullptr)
+        for (int b = 0; b < 3; ++b)
+          for (int a = 0; a < 3; ++a) {
+            const double f = q2v(a, gq(qx)) * q2v(b, gq(qy));
+            const size_t gn = (size_t)(2 * ey + b) * N + 2 * ex + a;
+            a0 += f * w[gn];
+            a1 += f * w[gn + nv];
+          }
+      wq[0][qy * 3 + qx] = a0;
+      wq[1][qy * 3 + qx] = a1;
+    }
+  const double dl = sd_delta<double>(N, nv, ex, ey, w, fmax(hx, hy), nu, sdc);
+  for (int ti = 0; ti < 9; ++ti) {
+    const int ai = ti % 3, bi = ti / 3;
+    const int gi = 2 * ex + ai, gj = 2 * ey + bi;
+    if (gi == 0 || gj == 0 || gi == N - 1 || gj == N - 1) continue;
+    const int row = (gj - 1) * (N - 2) + (gi - 1);
+    for (int tj = 0; tj < 9; ++tj) {
+      const int aj = tj % 3, bj = tj / 3;
+      const int hi = 2 * ex + aj, hj = 2 * ey + bj;
+      if (hi == 0 || hj == 0 || hi == N - 1 || hj == N - 1) continue;
+      const int col = (hj - 1) * (N - 2) + (hi - 1);
+      double s = 0;
+      for (int qy = 0; qy < 3; ++qy)
+        for (int qx = 0; qx < 3; ++qx) {
+          const double W = gw(qx) * gw(qy) * hx * hy;
+          const double phi = q2v(ai, gq(qx)) * q2v(bi, gq(qy));
+          const double dxi = q2d(ai, gq(qx)) * q2v(bi, gq(qy)) / hx, dyi = q2v(ai, gq(qx)) * q2d(bi, gq(qy)) / hy;
+          const double dxj = q2d(aj, gq(qx)) * q2v(bj, gq(qy)) / hx, dyj = q2v(aj, gq(qx)) * q2d(bj, gq(qy)) / hy;
+          const double wgj = wq[0][qy * 3 + qx] * dxj + wq[1][qy * 3 + qx] * dyj;
+          const double wgi = wq[0][qy * 3 + qx] * dxi + wq[1][qy * 3 + qx] * dyi;
+          s += W * (nu * (dxi * dxj + dyi * dyj) + wgj * phi + dl * wgi * wgj);
+        }
+      atomicAdd(&D[(size_t)row * m + col], s);
+    }
+  }
+}
+
+// x(interior) = Ainv * b(interior) per component (blockIdx.y), Q2 lattice.
+template <class T>
+__global__ void k_q2_dense_mv(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, const int* done) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char sm[];
+  T* sb = reinterpret_cast<T*>(sm);
+  const int N = 2 * n + 1, M = N - 2, m = M * M;
+  const size_t off = (size_t)blockIdx.y * N * N;
+  for (int k = threadIdx.x; k < m; k += blockDim.x) sb[k] = b[off + (size_t)(k / M + 1) * N + (k % M + 1)];
+  __syncthreads();
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    T s = 0;
+    const T* row = Ainv + (size_t)r * m;
+    for (int k = 0; k < m; ++k) s += row[k] * sb[k];
+    x[off + (size_t)(r / M + 1) * N + (r % M + 1)] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// pressure (Q1 Laplacian) level kernels
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_q1_diag_lap(int n, double hx, double hy, T* __restrict__ dinv) {
+  const int M = n + 1;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < M * M; node += gridDim.x * blockDim.x) {
+    const int J = node / M, I = node - J * M;
+    const int ne = ((I > 0) + (I < n)) * ((J > 0) + (J < n));
+    dinv[node] = (T)(1.0 / (ne * (hy / hx + hx / hy) / 3.0));
+  }
+}
+
+template <class T>
+__global__ void k_q1_restrict(int nc, const T* __restrict__ rf, T* __restrict__ bc, const int* done) {
+  if (done != nullptr && *done) return;
+  const int Mc = nc + 1, Mf = 2 * nc + 1;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Mc * Mc; node += gridDim.x * blockDim.x) {
+    const int J = node / Mc, I = node - J * Mc;
+    T s = 0;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int j = 2 * J + dy;
+      if (j < 0 || j >= Mf) continue;
+      const T wyv = dy == 0 ? T(1) : T(0.5);
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int i = 2 * I + dx;
+        if (i < 0 || i >= Mf) continue;
+        s += wyv * (dx == 0 ? T(1) : T(0.5)) * rf[(size_t)j * Mf + i];
+      }
+    }
+    bc[node] = s;
+  }
+}
+
+template <class T>
+__global__ void k_q1_prolong_add(int nc, const T* __restrict__ xc, T* __restrict__ xf, const int* done) {
+  if (done != nullptr && *done) return;
+  const int Mc = nc + 1, Mf = 2 * nc + 1;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Mf * Mf; node += gridDim.x * blockDim.x) {
+    const int j = node / Mf, i = node - j * Mf;
+    const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
+    const T v = T(0.25) * (xc[(size_t)J0 * Mc + I0] + xc[(size_t)J0 * Mc + I1] + xc[(size_t)J1 * Mc + I0] + xc[(size_t)J1 * Mc + I1]);
+    xf[node] += v;
+  }
+}
+
+template <class T>
+__global__ void k_q1_jacobi0(int n, T omega, const T* __restrict__ dinv, const T* __restrict__ b, T* __restrict__ x, const int* done) {
+  if (done != nullptr && *done) return;
+  const int tot = (n + 1) * (n + 1);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < tot; k += gridDim.x * blockDim.x) x[k] = omega * dinv[k] * b[k];
+}
+
+template <class T>
+__global__ void k_dense_mv(int m, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, const int* done) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char sm[];
+  T* sb = reinterpret_cast<T*>(sm);
+  for (int k = threadIdx.x; k < m; k += blockDim.x) sb[k] = b[k];
+  __syncthreads();
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    T s = 0;
+    const T* row = Ainv + (size_t)r * m;
+    for (int k = 0; k < m; ++k) s += row[k] * sb[k];
+    x[r] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host: dense inverse by Gauss-Jordan with partial pivoting (set-up only)
+// ---------------------------------------------------------------------------
+static bool invert(std::vector<double>& A, int m) {
+  std::vector<double> I((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) I[(size_t)i * m + i] = 1.0;
+  for (int c = 0; c < m; ++c) {
+    int p = c;
+    double best = std::fabs(A[(size_t)c * m + c]);
+    for (int r = c + 1; r < m; ++r)
+      if (std::fabs(A[(size_t)r * m + c]) > best) { best = std::fabs(A[(size_t)r * m + c]); p = r; }
+    if (best == 0.0) return false;
+    if (p != c)
+      for (int k = 0; k < m; ++k) { std::swap(A[(size_t)p * m + k], A[(size_t)c * m + k]); std::swap(I[(size_t)p * m + k], I[(size_t)c * m + k]); }
+    const double inv = 1.0 / A[(size_t)c * m + c];
+    for (int k = 0; k < m; ++k) { A[(size_t)c * m + k] *= inv; I[(size_t)c * m + k] *= inv; }
+    for (int r = 0; r < m; ++r) {
+      if (r == c) continue;
+      const double f = A[(size_t)r * m + c];
+      if (f == 0.0) continue;
+      for (int k = 0; k < m; ++k) { A[(size_t)r * m + k] -= f * A[(size_t)c * m + k]; I[(size_t)r * m + k] -= f * I[(size_t)c * m + k]; }
+    }
+  }
+  A.swap(I);
+  return true;
+}
+
+template <class T>
+static eth_status upload(const std::vector<double>& h, T** d, cudaStream_t s) {
+  std::vector<T> t(h.begin(), h.end());
+  ETH_CUDA(cudaMalloc((void**)d, t.size() * sizeof(T)));
+  ETH_CUDA(cudaMemcpyAsync(*d, t.data(), t.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  ETH_CUDA(cudaStreamSynchronize(s));
+  return ETH_OK;
+}
+
+template <class T>
+void mg_free(Hier<T>& H) {
+  for (auto& L : H.lv) {
+    cudaFree(L.w); cudaFree(L.dinv); cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); cudaFree(L.t); cudaFree(L.conv);
+  }
+  H.lv.clear();
+  cudaFree(H.coarse_inv);
+  H.coarse_inv = nullptr;
+  H.built = false;
+}
+
+static int gsize(size_t work) {
+  size_t b = (work + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// levels n, n/2, ... while the size stays even and above nmin
+static std::vector<int> level_sizes(int n, int nmin) {
+  std::vector<int> ns{n};
+  while (ns.back() % 2 == 0 && ns.back() / 2 >= nmin && ns.back() / 2 >= 2) ns.push_back(ns.back() / 2);
+  return ns;
+}
+
+template <class T>
+eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art) {
+  mg_free(H);
+  const std::vector<int> ns = level_sizes(g->n, nmin);
+  if (ns.back() > 32) { set_error("multigrid: n=%d does not coarsen to <= 32 (n must be c*2^k, c <= 32)", g->n); return ETH_EINVAL; }
+  const bool conv = g->kind == ETH_OSEEN;
+  double wmax = 0.0;
+  if (conv) {
+    std::vector<double> wh(2 * (size_t)g->nv);
+    ETH_CUDA(cudaMemcpyAsync(wh.data(), g->wind, wh.size() * 8, cudaMemcpyDeviceToHost, g->s));
+    ETH_CUDA(cudaStreamSynchronize(g->s));
+    for (size_t k = 0; k < (size_t)g->nv; ++k) wmax = std::fmax(wmax, std::sqrt(wh[k] * wh[k] + wh[k + g->nv] * wh[k + g->nv]));
+  }
+  H.q1 = false;
+  H.omega = 0.85;
+  for (size_t l = 0; l < ns.size(); ++l) {
+    Level<T> L;
+    L.n = ns[l];
+    L.hx = g->hx * (g->n / L.n);
+    L.hy = g->hy * (g->n / L.n);
+    L.nu = g->nu;
+    L.sd = (l > 0 && conv) ? art : 0.0;
+    const size_t N = 2 * (size_t)L.n + 1, nv = N * N;
+    ETH_CUDA(cudaMalloc((void**)&L.dinv, nv * sizeof(T)));
+    ETH_CUDA(cudaMalloc((void**)&L.x, 2 * nv * sizeof(T)));
+    ETH_CUDA(cudaMalloc((void**)&L.b, 2 * nv * sizeof(T)));
+    ETH_CUDA(cudaMalloc((void**)&L.r, 2 * nv * sizeof(T)));
+    ETH_CUDA(cudaMalloc((void**)&L.t, 2 * nv * sizeof(T)));
+    ETH_CUDA(cudaMemsetAsync(L.x, 0, 2 * nv * sizeof(T), g->s));
+    ETH_CUDA(cudaMemsetAsync(L.t, 0, 2 * nv * sizeof(T), g->s));
+    if (conv) {
+      ETH_CUDA(cudaMalloc((void**)&L.w, 2 * nv * sizeof(T)));
+      if (l == 0) {
+        k_cast_from_f64<T><<<gsize(2 * nv), 256, 0, g->s>>>(2 * nv, g->wind, L.w);
+      } else {
+        k_q2_inject<T><<<gsize(nv), 256, 0, g->s>>>(L.n, H.lv[l - 1].w, L.w);
+      }
+      ETH_CUDA(cudaGetLastError());
+    }
+    k_q2_diag<T><<<gsize(nv), 256, 0, g->s>>>(L.n, L.hx, L.hy, L.nu, L.sd, L.w, L.dinv);
+    ETH_CUDA(cudaGetLastError());
+    H.lv.push_back(L);
+  }
+  // coarsest: dense inverse of the interior scalar operator
+  Level<T>& C = H.lv.back();
+  const int Nc = 2 * C.n + 1, m = (Nc - 2) * (Nc - 2);
+  double* D = nullptr;
+  double* wd = nullptr;
+  ETH_CUDA(cudaMalloc((void**)&D, (size_t)m * m * 8));
+  ETH_CUDA(cudaMemsetAsync(D, 0, (size_t)m * m * 8, g->s));
+  if (conv) {
+    ETH_CUDA(cudaMalloc((void**)&wd, 2 * (size_t)Nc * Nc * 8));
+    k_f64_from<T><<<gsize(2 * (size_t)Nc * Nc), 256, 0, g->s>>>(2 * (size_t)Nc * Nc, C.w, wd);
+  }
+  k_q2_coarse_mat<<<cdiv((long)C.n * C.n, 64), 64, 0, g->s>>>(C.n, C.hx, C.hy, C.nu, C.sd, wd, D);
+  ETH_CUDA(cudaGetLastError());
+  std::vector<double> h((size_t)m * m);
+  ETH_CUDA(cudaMemcpyAsync(h.data(), D, h.size() * 8, cudaMemcpyDeviceToHost, g->s));
+  ETH_CUDA(cudaStreamSynchronize(g->s));
+  cudaFree(D);
+  cudaFree(wd);
+  if (!invert(h, m)) { set_error("multigrid: singular coarse operator"); return ETH_EINVAL; }
+  ETH_TRY(upload<T>(h, &H.coarse_inv, g->s));
+  H.ncoarse = m;
+  H.built = true;
+  return ETH_OK;
+}
+
+template <class T>
+eth_status mg_build_q1(eth_grid* g, Hier<T>& H, int nmin) {
+  mg_free(H);
+  const std::vector<int> ns = level_sizes(g->n, nmin);
+  if (ns.back() > 32) { set_error("multigrid: n=%d does not coarsen to <= 32", g->n); return ETH_EINVAL; }
+  H.q1 = true;
+  H.omega = 0.85;
+  for (size_t l = 0; l < ns.size(); ++l) {
+    Level<T> L;
+    L.n = ns[l];
+    L.hx = g->hx * (g->n / L.n);
+    L.hy = g->hy * (g->n / L.n);
+    const size_t M = (size_t)L.n + 1, tot = M * M;
+    ETH_CUDA(cudaMalloc((void**)&L.dinv, tot * sizeof(T)));
+    ETH_CUDA(cudaMalloc((void**)&L.x, tot * sizeof(T)));
+    ETH_CUDA(cudaMalloc((void**)&L.b, tot * sizeof(T)));
+    ETH_CUDA(cudaMalloc((void**)&L.r, tot * sizeof(T)));
+    ETH_CUDA(cudaMalloc((void**)&L.t, tot * sizeof(T)));
+    k_q1_diag_lap<T><<<gsize(tot), 256, 0, g->s>>>(L.n, L.hx, L.hy, L.dinv);
+    ETH_CUDA(cudaGetLastError());
+    H.lv.push_back(L);
+  }
+  // coarsest: pseudo-inverse of K1 = (K1 + J/m)^{-1} - J/m, J = ones
+  const Level<T>& C = H.lv.back();
+  const int nc = C.n, M = nc + 1, m = M * M;
+  std::vector<double> K((size_t)m * m, 0.0);
+  const double rxy = C.hy / C.hx, ryx = C.hx / C.hy;
+  auto km = [](int a, int b) { return a == b ? 1.0 / 3.0 : 1.0 / 6.0; };
+  auto kk = [](int a, int b) { return a == b ? 1.0 : -1.0; };
+  for (int ey = 0; ey < nc; ++ey)
+    for (int ex = 0; ex < nc; ++ex)
+      for (int d = 0; d < 2; ++d)
+        for (int c = 0; c < 2; ++c)
+          for (int dd = 0; dd < 2; ++dd)
+            for (int cc = 0; cc < 2; ++cc) {
+              const int r = (ey + d) * M + ex + c, q = (ey + dd) * M + ex + cc;
+              K[(size_t)r * m + q] += rxy * kk(c, cc) * km(d, dd) + ryx * km(c, cc) * kk(d, dd);
+            }
+  for (size_t k = 0; k < K.size(); ++k) K[k] += 1.0 / m;
+  if (!invert(K, m)) { set_error("multigrid: singular Q1 coarse operator"); return ETH_EINVAL; }
+  for (size_t k = 0; k < K.size(); ++k) K[k] -= 1.0 / m;
+  ETH_TRY(upload<T>(K, &H.coarse_inv, g->s));
+  H.ncoarse = m;
+  H.built = true;
+  return ETH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycles
+// ---------------------------------------------------------------------------
+template <class T, class TO, int EPI, int CF>
+static eth_status q2_level(eth_grid* g, const Level<T>& L, const T* x, TO* y, T omega, const double* bsrc,
+                           const int* done, const Slot* slot, int slot_off, const double* dv) {
+  constexpr int F0 = QF_DIFF | QF_XIN | QF_UOUT | CF;
+  Q2Params<T, TO, T> P{};
+  P.n = L.n; P.hx = (T)L.hx; P.hy = (T)L.hy; P.nu = (T)L.nu; P.sd = (T)L.sd;
+  P.x = x; P.w = L.w; P.y = y; P.b = L.b; P.dinv = L.dinv; P.omega = omega; P.bsrc = bsrc; P.done = done;
+  if (slot) {
+    P.slot = *slot; P.slot_off = slot_off; P.dv = dv;
+    ETH_CUDA((launch_q2<T, TO, T, F0 | QF_DOT, EPI>(P, g->s)));
+  } else {
+    ETH_CUDA((launch_q2<T, TO, T, F0, EPI>(P, g->s)));
+  }
+  g->launches++;
+  return ETH_OK;
+}
+
+template <class T, class TO, int EPI>
+static eth_status q2_level_d(eth_grid* g, const Level<T>& L, const T* x, TO* y, T omega, const double* bsrc,
+                             const int* done, const Slot* slot = nullptr, int slot_off = 0, const double* dv = nullptr) {
+  if (L.w != nullptr && L.sd > 0.0) return q2_level<T, TO, EPI, QF_CONV | QF_SD>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
+  if (L.w != nullptr) return q2_level<T, TO, EPI, QF_CONV>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
+  return q2_level<T, TO, EPI, 0>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
+}
+
+int vel_final_blocks(int n) { return q2_blocks(n); }
+
+template <class T>
+eth_status vcycle_vel(eth_grid* g, Hier<T>& H, const double* v, double* z, int pre, int post, const int* done,
+                      const Slot* slot, int slot_off) {
+  const int nl = (int)H.lv.size();
+  const T om = (T)H.omega;
+  if (nl < 2) { set_error("vcycle: hierarchy needs two levels"); return ETH_EINVAL; }
+  // descend
+  for (int l = 0; l < nl - 1; ++l) {
+    Level<T>& L = H.lv[l];
+    const size_t N = 2 * (size_t)L.n + 1, nv = N * N;
+    if (l == 0)
+      k_q2_jacobi0<double, T><<<gsize(2 * nv), 256, 0, g->s>>>(L.n, om, L.dinv, v, L.b, L.x, done);
+    else
+      k_q2_jacobi0<T, T><<<gsize(2 * nv), 256, 0, g->s>>>(L.n, om, L.dinv, L.b, L.b, L.x, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+    T* cur = L.x;
+    T* oth = L.t;
+    for (int s = 1; s < pre; ++s) {
+      ETH_TRY((q2_level_d<T, T, EPI_SMOOTH>(g, L, cur, oth, om, nullptr, done)));
+      std::swap(cur, oth);
+    }
+    if (cur != L.x) {  // keep the iterate in L.x
+      ETH_CUDA(cudaMemcpyAsync(L.x, cur, 2 * nv * sizeof(T), cudaMemcpyDeviceToDevice, g->s));
+    }
+    ETH_TRY((q2_level_d<T, T, EPI_RESID>(g, L, L.x, L.r, om, nullptr, done)));
+    const Level<T>& Cn = H.lv[l + 1];
+    const size_t Nc = 2 * (size_t)Cn.n + 1;
+    k_q2_restrict<T><<<gsize(Nc * Nc), 256, 0, g->s>>>(Cn.n, L.r, Cn.b, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+  }
+  {  // coarse solve
+    Level<T>& C = H.lv[nl - 1];
+    const int m = H.ncoarse;
+    k_q2_dense_mv<T><<<dim3(cdiv(m, 128), 2), 128, m * sizeof(T), g->s>>>(C.n, H.coarse_inv, C.b, C.x, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+  }
+  // ascend
+  for (int l = nl - 2; l >= 0; --l) {
+    Level<T>& L = H.lv[l];
+    const Level<T>& Cn = H.lv[l + 1];
+    const size_t N = 2 * (size_t)L.n + 1;
+    k_q2_prolong_add<T><<<gsize(N * N), 256, 0, g->s>>>(Cn.n, Cn.x, L.x, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+    T* cur = L.x;
+    T* oth = L.t;
+    for (int s = 0; s < post; ++s) {
+      const bool last = (l == 0 && s == post - 1);
+      if (last) {
+        ETH_TRY((q2_level_d<T, double, EPI_SMOOTH>(g, L, cur, z, om, v, done, slot, slot_off, v)));
+      } else {
+        ETH_TRY((q2_level_d<T, T, EPI_SMOOTH>(g, L, cur, oth, om, nullptr, done)));
+        std::swap(cur, oth);
+      }
+    }
+    if (l > 0 && cur != L.x) {
+      const size_t nv = N * N;
+      ETH_CUDA(cudaMemcpyAsync(L.x, cur, 2 * nv * sizeof(T), cudaMemcpyDeviceToDevice, g->s));
+    }
+  }
+  return ETH_OK;
+}
+
+template <class T>
+static eth_status q1_level(eth_grid* g, const Level<T>& L, const T* x, T* y, int epi, T omega, const int* done) {
+  Q1Params<T, T, T> P{};
+  P.n = L.n; P.hx = (T)L.hx; P.hy = (T)L.hy; P.cm = 0; P.ck = 1; P.c1 = 0;
+  P.x = x; P.y = y; P.b = L.b; P.dinv = L.dinv; P.omega = omega; P.done = done;
+  if (epi == Q1E_SMOOTH) k_q1node<T, T, T, Q1E_SMOOTH><<<q1_blocks(L.n), 256, 0, g->s>>>(P);
+  else k_q1node<T, T, T, Q1E_RESID><<<q1_blocks(L.n), 256, 0, g->s>>>(P);
+  ETH_CUDA(cudaGetLastError());
+  g->launches++;
+  return ETH_OK;
+}
+
+template <class T>
+eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done) {
+  const int nl = (int)H.lv.size();
+  const T om = (T)H.omega;
+  for (int l = 0; l < nl - 1; ++l) {
+    Level<T>& L = H.lv[l];
+    const size_t tot = (size_t)(L.n + 1) * (L.n + 1);
+    if (l > 0) {
+      k_q1_jacobi0<T><<<gsize(tot), 256, 0, g->s>>>(L.n, om, L.dinv, L.b, L.x, done);
+      ETH_CUDA(cudaGetLastError());
+      g->launches++;
+    }
+    for (int s = 1; s < pre; ++s) {
+      ETH_TRY(q1_level<T>(g, L, L.x, L.t, Q1E_SMOOTH, om, done));
+      ETH_CUDA(cudaMemcpyAsync(L.x, L.t, tot * sizeof(T), cudaMemcpyDeviceToDevice, g->s));
+    }
+    ETH_TRY(q1_level<T>(g, L, L.x, L.r, Q1E_RESID, om, done));
+    const Level<T>& Cn = H.lv[l + 1];
+    k_q1_restrict<T><<<gsize((size_t)(Cn.n + 1) * (Cn.n + 1)), 256, 0, g->s>>>(Cn.n, L.r, Cn.b, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+  }
+  {
+    Level<T>& C = H.lv[nl - 1];
+    const int m = H.ncoarse;
+    k_dense_mv<T><<<cdiv(m, 128), 128, m * sizeof(T), g->s>>>(m, H.coarse_inv, C.b, C.x, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    Level<T>& L = H.lv[l];
+    const Level<T>& Cn = H.lv[l + 1];
+    const size_t tot = (size_t)(L.n + 1) * (L.n + 1);
+    k_q1_prolong_add<T><<<gsize(tot), 256, 0, g->s>>>(Cn.n, Cn.x, L.x, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+    for (int s = 0; s < post; ++s) {
+      ETH_TRY(q1_level<T>(g, L, L.x, L.t, Q1E_SMOOTH, om, done));
+      ETH_CUDA(cudaMemcpyAsync(L.x, L.t, tot * sizeof(T), cudaMemcpyDeviceToDevice, g->s));
+    }
+  }
+  return ETH_OK;
+}
+
+#define ETH_MG_INST(T)                                                                                    \
+  template eth_status mg_build_vel<T>(eth_grid*, Hier<T>&, int, double);                                 \
+  template eth_status mg_build_q1<T>(eth_grid*, Hier<T>&, int);                                          \
+  template void mg_free<T>(Hier<T>&);                                                                    \
+  template eth_status vcycle_vel<T>(eth_grid*, Hier<T>&, const double*, double*, int, int, const int*,   \
+                                    const Slot*, int);                                                   \
+  template eth_status vcycle_q1_from<T>(eth_grid*, Hier<T>&, int, int, const int*);
+ETH_MG_INST(float)
+ETH_MG_INST(double)
+
+}  // namespace eth

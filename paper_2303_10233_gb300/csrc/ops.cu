@@ -1,0 +1,169 @@
+// Operator applies of the public ABI (eth_apply) and right-hand-side assembly.
+#include "ops.cuh"
+
+namespace eth {
+
+Slot make_slot(eth_grid* g, int which, int total) {
+  Slot s;
+  s.part = g->part + (size_t)which * g->part_cap;
+  s.ticket = g->ticket + which;
+  s.out = &g->sc->dots[which];
+  s.total = total;
+  s.op = FIN_STORE;
+  s.sc = g->sc;
+  return s;
+}
+
+template <class CT>
+static const CT* wind_ptr(eth_grid* g);
+template <>
+const float* wind_ptr<float>(eth_grid* g) { return g->windf; }
+template <>
+const double* wind_ptr<double>(eth_grid* g) { return g->wind; }
+
+// y = K x with the velocity block F (Stokes: nu*A, Oseen: nu*A + N) --------
+template <class CT, int F>
+static eth_status run_q2(eth_grid* g, const double* x, const double* p, double* y, double* yp,
+                         const int* done = nullptr, Slot* slot = nullptr, int slot_off = 0) {
+  Q2Params<double, double, CT> P{};
+  P.n = g->n; P.hx = (CT)g->hx; P.hy = (CT)g->hy; P.nu = (CT)g->nu;
+  P.x = x; P.p = p; P.w = wind_ptr<CT>(g); P.y = y; P.yp = yp;
+  P.done = done;
+  if (slot) { P.slot = *slot; P.slot_off = slot_off; P.dv = x; P.dvp = p; }
+  ETH_CUDA((launch_q2<double, double, CT, F, EPI_APPLY>(P, g->s)));
+  g->launches++;
+  return ETH_OK;
+}
+
+template <class CT>
+static eth_status apply_t(eth_grid* g, eth_op op, const double* x, double* y) {
+  const bool conv = g->kind == ETH_OSEEN;
+  const size_t nu2 = 2 * (size_t)g->nv;
+  switch (op) {
+    case ETH_OP_K:
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+    case ETH_OP_KT:
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+    case ETH_OP_K1:
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+    case ETH_OP_A:
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_UOUT>(g, x, nullptr, y, nullptr);
+    case ETH_OP_F:
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_UOUT>(g, x, nullptr, y, nullptr);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_UOUT>(g, x, nullptr, y, nullptr);
+    case ETH_OP_B:
+      return run_q2<CT, QF_XIN | QF_P0 | QF_POUT>(g, x, nullptr, nullptr, y);
+    case ETH_OP_BT:
+      return run_q2<CT, QF_PIN | QF_P0 | QF_UOUT>(g, nullptr, x, y, nullptr);
+    case ETH_OP_MV:
+      return run_q2<CT, QF_MASS | QF_XIN | QF_UOUT | QF_NOBC>(g, x, nullptr, y, nullptr);
+    case ETH_OP_MQ: {
+      Q1Params<double, double, CT> P{};
+      P.n = g->n; P.hx = (CT)g->hx; P.hy = (CT)g->hy;
+      P.cm = 1; P.ck = 0; P.c1 = 0; P.x = x; P.x0 = x + g->n1; P.r0 = 1; P.y = y;
+      k_q1node<double, double, CT, Q1E_APPLY><<<q1_blocks(g->n), 256, 0, g->s>>>(P);
+      ETH_CUDA(cudaGetLastError());
+      k_p0rows<double, double, CT><<<cdiv((long)g->n0, 256), 256, 0, g->s>>>(
+          g->n, (CT)(g->hx * g->hy), (CT)1, (CT)1, x, x + g->n1, y + g->n1, nullptr);
+      ETH_CUDA(cudaGetLastError());
+      g->launches += 2;
+      return ETH_OK;
+    }
+  }
+  set_error("eth_apply: unknown operator %d", (int)op);
+  return ETH_EINVAL;
+}
+
+eth_status op_apply(eth_grid* g, eth_op op, bool fp32, const double* x, double* y) {
+  return fp32 ? apply_t<float>(g, op, x, y) : apply_t<double>(g, op, x, y);
+}
+
+// K z with the fused FP64 dot <Kz, z> into slot `which` (MINRES delta) ----
+template <class CT>
+static eth_status apply_dot_t(eth_grid* g, bool trans, const double* x, double* y, Slot s, const int* done) {
+  const bool conv = g->kind == ETH_OSEEN;
+  const size_t nu2 = 2 * (size_t)g->nv;
+  s.total = q2_blocks(g->n);
+  if (conv && trans)
+    return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT>(g, x, x + nu2, y, y + nu2, done, &s);
+  if (conv)
+    return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT>(g, x, x + nu2, y, y + nu2, done, &s);
+  return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT>(g, x, x + nu2, y, y + nu2, done, &s);
+}
+
+eth_status op_apply_K_dot(eth_grid* g, bool fp32, bool trans, const double* x, double* y, Slot s, const int* done) {
+  return fp32 ? apply_dot_t<float>(g, trans, x, y, s, done) : apply_dot_t<double>(g, trans, x, y, s, done);
+}
+
+eth_status op_apply_K(eth_grid* g, bool fp32, bool trans, const double* x, double* y, const int* done) {
+  const bool conv = g->kind == ETH_OSEEN;
+  const size_t nu2 = 2 * (size_t)g->nv;
+  if (fp32) {
+    if (conv && trans) return run_q2<float, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+    if (conv) return run_q2<float, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+    return run_q2<float, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+  }
+  if (conv && trans) return run_q2<double, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+  if (conv) return run_q2<double, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+  return run_q2<double, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+}
+
+// ---------------------------------------------------------------------------
+// right-hand side: b = [D_I (M f - F u_b) + D_B u_b ; -B u_b]
+// ---------------------------------------------------------------------------
+__global__ void k_rhs_combine(int n, const double* __restrict__ mf, const double* __restrict__ fub,
+                              const double* __restrict__ ub, double* __restrict__ bu) {
+  const int N = 2 * n + 1;
+  const size_t nv = (size_t)N * N;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t g = k < nv ? k : k - nv;
+    const int j = (int)(g / N), i = (int)(g - (size_t)j * N);
+    const bool bnd = i == 0 || j == 0 || i == N - 1 || j == N - 1;
+    bu[k] = bnd ? ub[k] : mf[k] - fub[k];
+  }
+}
+
+__global__ void k_keep_boundary(int n, const double* __restrict__ src, double* __restrict__ dst) {
+  const int N = 2 * n + 1;
+  const size_t nv = (size_t)N * N;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t g = k < nv ? k : k - nv;
+    const int j = (int)(g / N), i = (int)(g - (size_t)j * N);
+    const bool bnd = i == 0 || j == 0 || i == N - 1 || j == N - 1;
+    dst[k] = bnd ? src[k] : 0.0;
+  }
+}
+
+__global__ void k_scale(size_t m, double a, double* __restrict__ x) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) x[k] *= a;
+}
+
+eth_status assemble_rhs(eth_grid* g, const double* f, const double* ubc) {
+  const size_t nu2 = 2 * (size_t)g->nv;
+  const unsigned nb = cdiv((long)nu2, 256) > 4096 ? 4096 : cdiv((long)nu2, 256);
+  k_keep_boundary<<<nb, 256, 0, g->s>>>(g->n, ubc, g->ubc);
+  ETH_CUDA(cudaGetLastError());
+  double* mf = g->tmp;
+  double* fub = g->tmp2;
+  // M f (no Dirichlet masking)
+  ETH_TRY((run_q2<double, QF_MASS | QF_XIN | QF_UOUT | QF_NOBC>(g, f, nullptr, mf, nullptr)));
+  // F u_b with the boundary-only field (no masking of the input)
+  if (g->kind == ETH_OSEEN) {
+    ETH_TRY((run_q2<double, QF_DIFF | QF_CONV | QF_XIN | QF_UOUT | QF_NOBC>(g, g->ubc, nullptr, fub, nullptr)));
+  } else {
+    ETH_TRY((run_q2<double, QF_DIFF | QF_XIN | QF_UOUT | QF_NOBC>(g, g->ubc, nullptr, fub, nullptr)));
+  }
+  k_rhs_combine<<<nb, 256, 0, g->s>>>(g->n, mf, fub, g->ubc, g->b);
+  ETH_CUDA(cudaGetLastError());
+  // g = -B u_b
+  ETH_TRY((run_q2<double, QF_XIN | QF_P0 | QF_POUT | QF_NOBC>(g, g->ubc, nullptr, nullptr, g->b + nu2)));
+  k_scale<<<cdiv((long)(g->n1 + g->n0), 256), 256, 0, g->s>>>((size_t)(g->n1 + g->n0), -1.0, g->b + nu2);
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 4;
+  return ETH_OK;
+}
+
+}  // namespace eth

@@ -1,0 +1,14 @@
+// Declarations shared by the translation units of the library.
+#pragma once
+#include "common.cuh"
+#include "grid.cuh"
+#include "q2tile.cuh"
+#include "q1ops.cuh"
+
+namespace eth {
+Slot make_slot(eth_grid* g, int which, int total);
+eth_status op_apply(eth_grid* g, eth_op op, bool fp32, const double* x, double* y);
+eth_status op_apply_K_dot(eth_grid* g, bool fp32, bool trans, const double* x, double* y, Slot s, const int* done);
+eth_status op_apply_K(eth_grid* g, bool fp32, bool trans, const double* x, double* y, const int* done);
+eth_status assemble_rhs(eth_grid* g, const double* f, const double* ubc);
+}  // namespace eth

@@ -1,0 +1,586 @@
+// Krylov drivers: preconditioned MINRES (Algorithm 1) for Stokes with the
+// block-diagonal preconditioner blkdiag(V-cycle(nu A), nu M_Q^+) (Eq. stokes_pre,
+// Sec. 2.2: the M_Q solve keeps z orthogonal to k), FP64 iterative refinement
+// around mixed-precision inner solves, and the public solve entry points.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include "solve.cuh"
+#include "mg.cuh"
+
+namespace eth {
+
+enum : int { SL_DELTA = 0, SL_VSUM = 1, SL_GAMMA = 2, SL_MQ = 3, SL_DONE = 4, SL_NORM = 5, SL_PSUM = 6, SL_GEN = 7 };
+
+struct Work {
+  Hier<float> vf, qf;
+  Hier<double> vd, qd;
+  double *x = nullptr, *d = nullptr, *r = nullptr, *Kz = nullptr, *bp = nullptr;
+  double *V[2] = {nullptr, nullptr}, *Z[2] = {nullptr, nullptr}, *W[2] = {nullptr, nullptr};
+  cudaStream_t s2 = nullptr;   // second branch (pressure block)
+  cudaStream_t sm = nullptr;   // internal main stream (capturable), joined to the user stream
+  cudaEvent_t evf = nullptr, evj = nullptr, evu = nullptr, t0 = nullptr, t1 = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int gkey = -1;
+  int nmin_built = -1;
+};
+
+static void work_free(void* p) {
+  Work* w = (Work*)p;
+  if (!w) return;
+  mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
+  cudaFree(w->x); cudaFree(w->d); cudaFree(w->r); cudaFree(w->Kz); cudaFree(w->bp);
+  for (int k = 0; k < 2; ++k) { cudaFree(w->V[k]); cudaFree(w->Z[k]); cudaFree(w->W[k]); }
+  if (w->gexec) cudaGraphExecDestroy(w->gexec);
+  if (w->s2) cudaStreamDestroy(w->s2);
+  if (w->sm) cudaStreamDestroy(w->sm);
+  if (w->evu) cudaEventDestroy(w->evu);
+  if (w->evf) cudaEventDestroy(w->evf);
+  if (w->evj) cudaEventDestroy(w->evj);
+  if (w->t0) cudaEventDestroy(w->t0);
+  if (w->t1) cudaEventDestroy(w->t1);
+  delete w;
+}
+
+void solver_free(eth_grid* g) {
+  if (g->ws && g->ws_free) g->ws_free(g->ws);
+  g->ws = nullptr;
+}
+
+eth_status solver_coefficients_changed(eth_grid* g) {
+  Work* w = (Work*)g->ws;
+  if (!w) return ETH_OK;
+  mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
+  if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; w->gkey = -1; }
+  return ETH_OK;
+}
+
+static eth_status work_get(eth_grid* g, Work** out) {
+  if (g->ws) { *out = (Work*)g->ws; return ETH_OK; }
+  Work* w = new Work();
+  g->ws = w;
+  g->ws_free = work_free;
+  const size_t nt = g->nt;
+  double** bufs[] = {&w->x, &w->d, &w->r, &w->Kz, &w->bp, &w->V[0], &w->V[1], &w->Z[0], &w->Z[1], &w->W[0], &w->W[1]};
+  for (double** b : bufs) ETH_CUDA(cudaMalloc((void**)b, nt * 8));
+  ETH_CUDA(cudaStreamCreateWithFlags(&w->s2, cudaStreamNonBlocking));
+  ETH_CUDA(cudaStreamCreateWithFlags(&w->sm, cudaStreamNonBlocking));
+  ETH_CUDA(cudaEventCreateWithFlags(&w->evu, cudaEventDisableTiming));
+  ETH_CUDA(cudaEventCreateWithFlags(&w->evf, cudaEventDisableTiming));
+  ETH_CUDA(cudaEventCreateWithFlags(&w->evj, cudaEventDisableTiming));
+  ETH_CUDA(cudaEventCreate(&w->t0));
+  ETH_CUDA(cudaEventCreate(&w->t1));
+  *out = w;
+  return ETH_OK;
+}
+
+static int vblocks(size_t m) {
+  size_t b = (m + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  return (int)(b < 1 ? 1 : b);
+}
+
+static Slot slot_of(eth_grid* g, int which, int total, int op) {
+  Slot s = make_slot(g, which, total);
+  s.op = op;
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 vector kernels (grid-stride, fused reductions through Slot)
+// ---------------------------------------------------------------------------
+__global__ void k_residual(size_t m, const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r, Slot sl) {
+  double acc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
+    const double v = b[k] - y[k];
+    r[k] = v;
+    acc += v * v;
+  }
+  double v[1] = {acc};
+  if (slot_arrive<1>(sl, blockIdx.x, v)) finish_slot(sl, v[0]);
+}
+
+// sums of the Q1 and P0 pressure blocks of x (length nt): FIN_STORE of (sum p1, sum p0)
+__global__ void k_psums(size_t off, size_t n1, size_t n0, const double* __restrict__ x, Slot sl) {
+  double a1 = 0.0, a0 = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1 + n0; k += (size_t)gridDim.x * blockDim.x) {
+    if (k < n1) a1 += x[off + k]; else a0 += x[off + k];
+  }
+  double v[2] = {a1, a0};
+  if (slot_arrive<2>(sl, blockIdx.x, v)) finish_slot_n<2>(sl, v);
+}
+
+// x_p1 -= sum_p1 / n1 ; x_p0 -= sum_p0 / n0  (sums in sums[0], sums[1])
+__global__ void k_psub(size_t off, size_t n1, size_t n0, double* __restrict__ x, const double* __restrict__ sums) {
+  const double m1 = sums[0] / (double)n1, m0 = sums[1] / (double)n0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1 + n0; k += (size_t)gridDim.x * blockDim.x)
+    x[off + k] -= k < n1 ? m1 : m0;
+}
+
+__global__ void k_add(size_t m, double* __restrict__ x, const double* __restrict__ d) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) x[k] += d[k];
+}
+
+__global__ void k_set_boundary(int n, double* __restrict__ u, const double* __restrict__ ub) {
+  const int N = 2 * n + 1;
+  const size_t nv = (size_t)N * N;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t gg = k < nv ? k : k - nv;
+    const int j = (int)(gg / N), i = (int)(gg - (size_t)j * N);
+    if (i == 0 || j == 0 || i == N - 1 || j == N - 1) u[k] = ub[k];
+  }
+}
+
+// MINRES v_{j+1} = VA K z_j - VB v_j - VC v_{j-1} (into vo); sums of its p1/p0 blocks.
+__global__ void k_minres_v(size_t nt, size_t nu2, size_t n1, const double* __restrict__ Kz, const double* __restrict__ vj,
+                           double* __restrict__ vo, const Scalars* __restrict__ sc, Slot sl) {
+  if (sc->done) return;
+  const double a = sc->v[S_VA], b = sc->v[S_VB], c = sc->v[S_VC];
+  double a1 = 0.0, a0 = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
+    const double v = a * Kz[k] - b * vj[k] - c * vo[k];
+    vo[k] = v;
+    if (k >= nu2) { if (k < nu2 + n1) a1 += v; else a0 += v; }
+  }
+  double v[2] = {a1, a0};
+  if (slot_arrive<2>(sl, blockIdx.x, v)) finish_slot_n<2>(sl, v);
+}
+
+// MINRES w_{j+1} = WZ z_j - WO w_{j-1} - WW w_j (into wo); x += XC w_{j+1}; last block: done = pending.
+__global__ void k_minres_wx(size_t nt, const double* __restrict__ zj, double* __restrict__ wo, const double* __restrict__ wj,
+                            double* __restrict__ x, Scalars* __restrict__ sc, Slot sl) {
+  if (sc->done) return;
+  const double cz = sc->v[S_WZ], co = sc->v[S_WO], cw = sc->v[S_WW], cx = sc->v[S_XC];
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
+    const double w = cz * zj[k] - co * wo[k] - cw * wj[k];
+    wo[k] = w;
+    x[k] += cx * w;
+  }
+  double v[1] = {0.0};
+  if (slot_arrive<1>(sl, blockIdx.x, v)) finish_slot(sl, 0.0);
+}
+
+__global__ void k_init_scalars(Scalars* sc, double tol, double n1, double n0, double mqc, double nu) {
+  for (int k = 0; k < S_LAST; ++k) sc->v[k] = 0.0;
+  sc->v[S_TOL] = tol;
+  sc->v[S_NP1] = n1;
+  sc->v[S_NP0] = n0;
+  sc->v[S_MQC] = mqc;
+  sc->v[S_MQNU] = nu;
+  sc->done = 0;
+  sc->status = 0;
+  sc->iter = 0;
+}
+
+// ---------------------------------------------------------------------------
+// pressure block: nu * M_Q^+ with k projected out (Sec. 2.2-2.3)
+//   r = v - beta k  (beta = k^T v / k^T k)
+//   t = r_k - R^T Q0^{-1} r_0            (t_I = r_k,I - 1/4 sum_{T ni I} r_0,T)
+//   z_k = c V_K1(t) + g1                  (S ~ h^2/16 K1, c = 16/|T|)
+//   z_0 = Q0^{-1}(r_0 - R z_k)
+//   g1 chosen so that k^T z = 0; output nu * z.
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void k_mq_t(int n, const double* __restrict__ vp, const Scalars* __restrict__ sc, T* __restrict__ b,
+                       T* __restrict__ x, const T* __restrict__ dinv, T omega, const int* done) {
+  if (done != nullptr && *done) return;
+  const int M = n + 1, n1 = M * M;
+  const double beta = sc->v[S_BETA];
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n1; node += gridDim.x * blockDim.x) {
+    const int J = node / M, I = node - J * M;
+    double s = 0.0;
+    for (int ey = J - 1; ey <= J; ++ey) {
+      if (ey < 0 || ey >= n) continue;
+      for (int ex = I - 1; ex <= I; ++ex) {
+        if (ex < 0 || ex >= n) continue;
+        s += vp[n1 + (size_t)ey * n + ex] + beta;
+      }
+    }
+    const T t = (T)(vp[node] - beta - 0.25 * s);
+    b[node] = t;
+    x[node] = omega * dinv[node] * t;
+  }
+}
+
+template <class T>
+__global__ void k_mq_sums(int n, const T* __restrict__ zt, const double* __restrict__ vp, double area, Slot sl, const int* done) {
+  if (done != nullptr && *done) return;
+  const int M = n + 1, n1 = M * M, n0 = n * n;
+  const double beta = sl.sc->v[S_BETA];
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n0; k += gridDim.x * blockDim.x) {
+    if (k < n1) {
+      const int J = k / M, I = k - J * M;
+      const int ne = ((I > 0) + (I < n)) * ((J > 0) + (J < n));
+      const double z = (double)zt[k];
+      s0 += z;
+      s1 += ne * z;
+    } else {
+      s2 += (vp[k] + beta) / area;
+    }
+  }
+  double v[3] = {s0, s1, s2};
+  if (slot_arrive<3>(sl, blockIdx.x, v)) finish_slot_n<3>(sl, v);
+}
+
+template <class T>
+__global__ void k_mq_out(int n, const T* __restrict__ zt, const double* __restrict__ vp, double* __restrict__ zp, double area,
+                         const Scalars* __restrict__ sc, Slot gsl, int goff, const int* done) {
+  if (done != nullptr && *done) return;
+  const int M = n + 1, n1 = M * M, n0 = n * n;
+  const double beta = sc->v[S_BETA], c = sc->v[S_MQC], g1 = sc->v[S_MQG], nu = sc->v[S_MQNU];
+  double acc = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n0; k += gridDim.x * blockDim.x) {
+    double z;
+    if (k < n1) {
+      z = nu * (c * (double)zt[k] + g1);
+    } else {
+      const int e = k - n1, ey = e / n, ex = e - ey * n;
+      const double s = (double)zt[(size_t)ey * M + ex] + (double)zt[(size_t)ey * M + ex + 1] +
+                       (double)zt[(size_t)(ey + 1) * M + ex] + (double)zt[(size_t)(ey + 1) * M + ex + 1];
+      z = nu * ((vp[k] + beta) / area - 0.25 * c * s - g1);
+    }
+    zp[k] = z;
+    acc += z * vp[k];
+  }
+  double v[1] = {acc};
+  if (slot_arrive<1>(gsl, goff + blockIdx.x, v)) finish_slot(gsl, v[0]);
+}
+
+static int mq_blocks(eth_grid* g) { return vblocks((size_t)g->n1 + g->n0); }
+
+template <class T>
+static eth_status precond_pressure(eth_grid* g, Hier<T>& Q, const double* vp, double* zp, const Slot& gsl, int goff,
+                                   const int* done, cudaStream_t s) {
+  Level<T>& L0 = Q.lv[0];
+  const cudaStream_t keep = g->s;
+  g->s = s;
+  k_mq_t<T><<<vblocks(g->n1), 256, 0, s>>>(g->n, vp, g->sc, L0.b, L0.x, L0.dinv, (T)Q.omega, done);
+  ETH_CUDA(cudaGetLastError());
+  eth_status st = vcycle_q1_from<T>(g, Q, 1, 1, done);
+  if (st != ETH_OK) { g->s = keep; return st; }
+  const int nb = mq_blocks(g);
+  Slot sm = slot_of(g, SL_MQ, nb, FIN_MQ);
+  k_mq_sums<T><<<nb, 256, 0, s>>>(g->n, L0.x, vp, g->hx * g->hy, sm, done);
+  ETH_CUDA(cudaGetLastError());
+  k_mq_out<T><<<nb, 256, 0, s>>>(g->n, L0.x, vp, zp, g->hx * g->hy, g->sc, gsl, goff, done);
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 3;
+  g->s = keep;
+  return ETH_OK;
+}
+
+template <class T>
+static Hier<T>& vel_hier(Work* w);
+template <>
+Hier<float>& vel_hier<float>(Work* w) { return w->vf; }
+template <>
+Hier<double>& vel_hier<double>(Work* w) { return w->vd; }
+template <class T>
+static Hier<T>& q1_hier(Work* w);
+template <>
+Hier<float>& q1_hier<float>(Work* w) { return w->qf; }
+template <>
+Hier<double>& q1_hier<double>(Work* w) { return w->qd; }
+
+// z = P^{-1} v with the fused <z, v> into the gamma slot (finisher fin).
+// The velocity V-cycle and the pressure block run on two streams (fork/join).
+template <class T>
+static eth_status precond_stokes(eth_grid* g, Work* w, const eth_opts* o, const double* v, double* z, int fin, const int* done) {
+  const size_t nu2 = 2 * (size_t)g->nv;
+  const int nbv = vel_final_blocks(g->n), nbp = mq_blocks(g);
+  Slot gs = slot_of(g, SL_GAMMA, nbv + nbp, fin);
+  ETH_CUDA(cudaEventRecord(w->evf, g->s));
+  ETH_CUDA(cudaStreamWaitEvent(w->s2, w->evf, 0));
+  ETH_TRY(precond_pressure<T>(g, q1_hier<T>(w), v + nu2, z + nu2, gs, nbv, done, w->s2));
+  ETH_TRY(vcycle_vel<T>(g, vel_hier<T>(w), v, z, o->mg_pre, o->mg_post, done, &gs, 0));
+  ETH_CUDA(cudaEventRecord(w->evj, w->s2));
+  ETH_CUDA(cudaStreamWaitEvent(g->s, w->evj, 0));
+  return ETH_OK;
+}
+
+// one MINRES iteration j (buffers by parity)
+template <class T>
+static eth_status minres_iter(eth_grid* g, Work* w, const eth_opts* o, bool fp32, int j) {
+  const size_t nt = g->nt, nu2 = 2 * (size_t)g->nv;
+  const int* done = &g->sc->done;
+  double* zj = w->Z[j & 1];
+  double* zn = w->Z[(j + 1) & 1];
+  double* vj = w->V[j & 1];
+  double* vo = w->V[(j + 1) & 1];
+  double* wj = w->W[j & 1];
+  double* wo = w->W[(j + 1) & 1];
+  ETH_TRY(op_apply_K_dot(g, fp32, false, zj, w->Kz, slot_of(g, SL_DELTA, 0, FIN_MINRES_DELTA), done));
+  const int nb = vblocks(nt);
+  k_minres_v<<<nb, 256, 0, g->s>>>(nt, nu2, (size_t)g->n1, w->Kz, vj, vo, g->sc, slot_of(g, SL_VSUM, nb, FIN_VSUMS));
+  ETH_CUDA(cudaGetLastError());
+  ETH_TRY(precond_stokes<T>(g, w, o, vo, zn, FIN_MINRES_GAMMA, done));
+  k_minres_wx<<<nb, 256, 0, g->s>>>(nt, zj, wo, wj, w->d, g->sc, slot_of(g, SL_DONE, nb, FIN_DONE));
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 2;
+  return ETH_OK;
+}
+
+static eth_status read_scalars(eth_grid* g) {
+  ETH_CUDA(cudaMemcpyAsync(g->sch, g->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->s));
+  ETH_CUDA(cudaStreamSynchronize(g->s));
+  return ETH_OK;
+}
+
+// Inner MINRES on K d = r (d from zero).  Returns iterations and device status.
+template <class T>
+static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp32, double tol, int maxit, int* its, int* dstat) {
+  const size_t nt = g->nt;
+  const double area = g->hx * g->hy;
+  k_init_scalars<<<1, 1, 0, g->s>>>(g->sc, tol, (double)g->n1, (double)g->n0, 16.0 / area, g->nu);
+  ETH_CUDA(cudaGetLastError());
+  ETH_CUDA(cudaMemsetAsync(w->d, 0, nt * 8, g->s));
+  ETH_CUDA(cudaMemsetAsync(w->W[0], 0, nt * 8, g->s));
+  ETH_CUDA(cudaMemsetAsync(w->W[1], 0, nt * 8, g->s));
+  ETH_CUDA(cudaMemsetAsync(w->V[0], 0, nt * 8, g->s));
+  ETH_CUDA(cudaMemcpyAsync(w->V[1], w->r, nt * 8, cudaMemcpyDeviceToDevice, g->s));
+  // beta of v_1 for the k-projection, then z_1 = P^{-1} v_1 and gamma_1
+  {
+    const int nb = vblocks((size_t)g->n1 + g->n0);
+    Slot s = slot_of(g, SL_VSUM, nb, FIN_VSUMS);
+    k_psums<<<nb, 256, 0, g->s>>>(2 * (size_t)g->nv, (size_t)g->n1, (size_t)g->n0, w->V[1], s);
+    ETH_CUDA(cudaGetLastError());
+  }
+  ETH_TRY(precond_stokes<T>(g, w, o, w->V[1], w->Z[1], FIN_MINRES_INIT, nullptr));
+  ETH_TRY(read_scalars(g));
+  if (g->sch->v[S_PEND] != 0.0) { *its = 0; *dstat = g->sch->status; return ETH_OK; }
+  int j = 1;
+  const bool use_graph = o->graph != 0;
+  const int key = (int)fp32 * 1000 + (int)(sizeof(T)) * 10 + o->mg_pre + 100 * o->mg_post;
+  while (true) {
+    if (use_graph) {
+      if (!w->gexec || w->gkey != key) {
+        if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; }
+        cudaGraph_t graph;
+        ETH_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
+        eth_status st = minres_iter<T>(g, w, o, fp32, 1);
+        if (st == ETH_OK) st = minres_iter<T>(g, w, o, fp32, 2);
+        cudaError_t ce = cudaStreamEndCapture(g->s, &graph);
+        if (st != ETH_OK) return st;
+        ETH_CUDA(ce);
+        ETH_CUDA(cudaGraphInstantiate(&w->gexec, graph, 0));
+        cudaGraphDestroy(graph);
+        w->gkey = key;
+      }
+      ETH_CUDA(cudaGraphLaunch(w->gexec, g->s));
+    } else {
+      ETH_TRY(minres_iter<T>(g, w, o, fp32, j));
+      ETH_TRY(minres_iter<T>(g, w, o, fp32, j + 1));
+    }
+    j += 2;
+    ETH_TRY(read_scalars(g));
+    if (g->sch->done || (int)g->sch->v[S_ITS] >= maxit) break;
+  }
+  *its = (int)g->sch->v[S_ITS];
+  *dstat = g->sch->status;
+  return ETH_OK;
+}
+
+template <class T>
+static eth_status ensure_hier(eth_grid* g, Work* w, const eth_opts* o) {
+  const int nmin = std::max(2, o->mg_min_n);
+  if (w->nmin_built != nmin) {
+    mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
+    if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; w->gkey = -1; }
+    w->nmin_built = nmin;
+  }
+  Hier<T>& V = vel_hier<T>(w);
+  Hier<T>& Q = q1_hier<T>(w);
+  if (!V.built) ETH_TRY(mg_build_vel<T>(g, V, nmin, 0.0));
+  if (!Q.built) ETH_TRY(mg_build_q1<T>(g, Q, nmin));
+  return ETH_OK;
+}
+
+// ||b - K x||^2 in FP64 (K applied with FP64 element arithmetic); result to host.
+static eth_status true_residual(eth_grid* g, Work* w, const double* b, double* rr) {
+  ETH_TRY(op_apply_K(g, false, false, w->x, w->Kz, nullptr));
+  const int nb = vblocks(g->nt);
+  k_residual<<<nb, 256, 0, g->s>>>((size_t)g->nt, b, w->Kz, w->r, slot_of(g, SL_NORM, nb, FIN_STORE));
+  ETH_CUDA(cudaGetLastError());
+  ETH_CUDA(cudaMemcpyAsync(&g->sch->dots[SL_NORM], &g->sc->dots[SL_NORM], 8, cudaMemcpyDeviceToHost, g->s));
+  ETH_CUDA(cudaStreamSynchronize(g->s));
+  *rr = g->sch->dots[SL_NORM];
+  g->launches += 1;
+  return ETH_OK;
+}
+
+// remove the e1 / e0 components of the pressure block of x (Euclidean)
+static eth_status canonicalize(eth_grid* g, double* x) {
+  const int nb = vblocks((size_t)g->n1 + g->n0);
+  const size_t off = 2 * (size_t)g->nv;
+  k_psums<<<nb, 256, 0, g->s>>>(off, (size_t)g->n1, (size_t)g->n0, x, slot_of(g, SL_PSUM, nb, FIN_STORE));
+  ETH_CUDA(cudaGetLastError());
+  k_psub<<<nb, 256, 0, g->s>>>(off, (size_t)g->n1, (size_t)g->n0, x, &g->sc->dots[SL_PSUM]);
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 2;
+  return ETH_OK;
+}
+
+template <class T>
+static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st) {
+  const size_t nt = g->nt;
+  const bool fp32 = o->precision == ETH_MIXED;
+  // consistent right-hand side: b with its e1 / e0 components removed
+  ETH_CUDA(cudaMemcpyAsync(w->bp, g->b, nt * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_TRY(canonicalize(g, w->bp));
+  ETH_CUDA(cudaMemcpyAsync(g->sch->dots, g->sc->dots, sizeof(g->sc->dots), cudaMemcpyDeviceToHost, g->s));
+  double bb = 0.0;
+  {
+    const int nb = vblocks(nt);
+    ETH_CUDA(cudaMemsetAsync(w->Kz, 0, nt * 8, g->s));
+    k_residual<<<nb, 256, 0, g->s>>>(nt, w->bp, w->Kz, w->r, slot_of(g, SL_NORM, nb, FIN_STORE));
+    ETH_CUDA(cudaGetLastError());
+    ETH_CUDA(cudaMemcpyAsync(&g->sch->dots[SL_NORM], &g->sc->dots[SL_NORM], 8, cudaMemcpyDeviceToHost, g->s));
+    ETH_CUDA(cudaStreamSynchronize(g->s));
+    bb = g->sch->dots[SL_NORM];
+  }
+  const double nb2 = std::sqrt(bb);
+  const double incons = std::sqrt(g->sch->dots[SL_PSUM] * g->sch->dots[SL_PSUM] / g->n1 +
+                                  g->sch->dots[SL_PSUM + 1] * g->sch->dots[SL_PSUM + 1] / g->n0);
+  eth_status result = ETH_OK;
+  if (nb2 > 0 && incons > 1e-8 * nb2) result = ETH_EINCONSISTENT;
+  if (!(nb2 > 0.0)) {  // zero right-hand side: x = 0
+    ETH_CUDA(cudaMemsetAsync(w->x, 0, nt * 8, g->s));
+    st->relres_true = 0.0;
+    return ETH_OK;
+  }
+  double rr;
+  ETH_TRY(true_residual(g, w, w->bp, &rr));
+  st->relres0 = std::sqrt(rr) / nb2;
+  double rel = st->relres0;
+  int total = 0, passes = 0;
+  const double inner_floor = fp32 ? o->refine_inner_tol : 0.0;
+  while (rel > o->tol && total < o->maxit) {
+    if (!std::isfinite(rel)) { result = ETH_ENAN; break; }
+    double itol = 0.3 * o->tol / rel;
+    itol = std::max(itol, inner_floor);
+    itol = std::min(itol, 0.5);
+    int its = 0, ds = 0;
+    ETH_TRY(minres_solve<T>(g, w, o, fp32, itol, o->maxit - total, &its, &ds));
+    total += its;
+    passes++;
+    const int nb = vblocks(nt);
+    k_add<<<nb, 256, 0, g->s>>>(nt, w->x, w->d);
+    ETH_CUDA(cudaGetLastError());
+    ETH_TRY(canonicalize(g, w->x));
+    ETH_TRY(true_residual(g, w, w->bp, &rr));
+    rel = std::sqrt(rr) / nb2;
+    if (o->verbose) fprintf(stderr, "[eth] pass %d: inner its %d (tol %.1e) relres %.3e status %d\n", passes, its, itol, rel, ds);
+    if (ds == ETH_EBREAKDOWN && its == 0) { result = ETH_EBREAKDOWN; break; }
+    if (its == 0) break;
+  }
+  st->iters_total = total;
+  st->iters_stage1 = total;
+  st->refine_passes = passes;
+  st->relres_true = rel;
+  if (result == ETH_OK && rel > o->tol) result = std::isfinite(rel) ? ETH_ENOTCONV : ETH_ENAN;
+  return result;
+}
+
+// Runs the solver body on the handle's internal stream (capturable even when
+// the user stream is the legacy default stream), ordered after and before the
+// user stream's work.
+struct StreamSwap {
+  eth_grid* g;
+  Work* w;
+  cudaStream_t user;
+  StreamSwap(eth_grid* g_, Work* w_) : g(g_), w(w_), user(g_->s) {
+    cudaEventRecord(w->evu, user);
+    cudaStreamWaitEvent(w->sm, w->evu, 0);
+    g->s = w->sm;
+  }
+  ~StreamSwap() {
+    cudaEventRecord(w->evu, w->sm);
+    cudaStreamWaitEvent(user, w->evu, 0);
+    g->s = user;
+  }
+};
+
+}  // namespace eth
+
+using namespace eth;
+
+extern "C" {
+
+eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, eth_stats* stats) {
+  if (!g || !u || !p) { set_error("eth_solve: NULL argument"); return ETH_EINVAL; }
+  if (!g->has_rhs) { set_error("eth_solve: no right-hand side (eth_set_rhs)"); return ETH_EINVAL; }
+  eth_opts o;
+  if (opts) o = *opts; else eth_default_opts(&o);
+  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1) { set_error("eth_solve: bad options"); return ETH_EINVAL; }
+  if (o.precision != ETH_FP64 && o.precision != ETH_MIXED) { set_error("eth_solve: bad precision"); return ETH_EINVAL; }
+  if (g->kind != ETH_STOKES) { set_error("eth_solve: Oseen solver not available in this build"); return ETH_EINVAL; }
+  eth_stats st;
+  std::memset(&st, 0, sizeof(st));
+  Work* w;
+  ETH_TRY(work_get(g, &w));
+  StreamSwap guard(g, w);
+  if (o.precision == ETH_MIXED) ETH_TRY(ensure_hier<float>(g, w, &o)); else ETH_TRY(ensure_hier<double>(g, w, &o));
+  const long l0 = g->launches;
+  ETH_CUDA(cudaEventRecord(w->t0, g->s));
+  const size_t nu2 = 2 * (size_t)g->nv;
+  ETH_CUDA(cudaMemcpyAsync(w->x, u, nu2 * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaMemcpyAsync(w->x + nu2, p, (size_t)(g->n1 + g->n0) * 8, cudaMemcpyDeviceToDevice, g->s));
+  k_set_boundary<<<vblocks(nu2), 256, 0, g->s>>>(g->n, w->x, g->ubc);
+  ETH_CUDA(cudaGetLastError());
+  eth_status r = o.precision == ETH_MIXED ? stokes_solve<float>(g, w, &o, &st) : stokes_solve<double>(g, w, &o, &st);
+  if (r == ETH_ECUDA || r == ETH_ENOMEM || r == ETH_EINVAL) return r;
+  ETH_CUDA(cudaMemcpyAsync(u, w->x, nu2 * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaMemcpyAsync(p, w->x + nu2, (size_t)(g->n1 + g->n0) * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaEventRecord(w->t1, g->s));
+  ETH_CUDA(cudaEventSynchronize(w->t1));
+  float ms = 0.f;
+  ETH_CUDA(cudaEventElapsedTime(&ms, w->t0, w->t1));
+  st.seconds = ms * 1e-3;
+  st.status = r;
+  st.kernel_launches = (int)(g->launches - l0);
+  if (stats) *stats = st;
+  return r;
+}
+
+eth_status eth_solve_host(eth_grid* g, const eth_opts* opts, const double* f, const double* ub, double* u, double* p,
+                          eth_stats* stats) {
+  if (!g || !f || !ub || !u || !p) { set_error("eth_solve_host: NULL argument"); return ETH_EINVAL; }
+  Work* w;
+  ETH_TRY(work_get(g, &w));
+  const size_t nu2 = 2 * (size_t)g->nv, np = (size_t)g->n1 + g->n0;
+  double *fd = w->Kz, *ud = w->r;   // staging: f and u_b (re-used scratch)
+  ETH_CUDA(cudaMemcpyAsync(fd, f, nu2 * 8, cudaMemcpyHostToDevice, g->s));
+  ETH_CUDA(cudaMemcpyAsync(ud, ub, nu2 * 8, cudaMemcpyHostToDevice, g->s));
+  ETH_TRY(eth_set_rhs(g, fd, ud));
+  double* uo = w->V[0];
+  double* po = w->V[1];
+  ETH_CUDA(cudaMemsetAsync(uo, 0, nu2 * 8, g->s));
+  ETH_CUDA(cudaMemsetAsync(po, 0, np * 8, g->s));
+  eth_status r = eth_solve(g, opts, uo, po, stats);
+  if (r != ETH_OK && r != ETH_ENOTCONV) return r;
+  ETH_CUDA(cudaMemcpyAsync(u, uo, nu2 * 8, cudaMemcpyDeviceToHost, g->s));
+  ETH_CUDA(cudaMemcpyAsync(p, po, np * 8, cudaMemcpyDeviceToHost, g->s));
+  ETH_CUDA(cudaStreamSynchronize(g->s));
+  return r;
+}
+
+eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* o, const double* ru, const double* rp, double* lu, double* lp, eth_stats* st) {
+  (void)g; (void)o; (void)ru; (void)rp; (void)lu; (void)lp; (void)st;
+  set_error("eth_solve_adjoint: not available in this build");
+  return ETH_EINVAL;
+}
+eth_status eth_batch_create(int count, eth_grid* const* grids, eth_batch** out) {
+  (void)count; (void)grids;
+  if (out) *out = nullptr;
+  set_error("eth_batch_create: not available in this build");
+  return ETH_EINVAL;
+}
+eth_status eth_batch_solve(eth_batch* b, const eth_opts* o, double* const* u, double* const* p, eth_stats* st) {
+  (void)b; (void)o; (void)u; (void)p; (void)st;
+  set_error("eth_batch_solve: not available in this build");
+  return ETH_EINVAL;
+}
+void eth_batch_destroy(eth_batch* b) { (void)b; }
+}

@@ -1,0 +1,222 @@
+"""Thin ctypes binding of the C ABI in ``include/eth.h`` (argument marshalling only).
+
+Every numerical step runs in the CUDA library ``_lib/libeth.so``; this module
+only converts torch tensors to device pointers and option dicts to the
+``eth_opts`` struct.  Importing it fails loudly when the library is missing:
+there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libeth.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "eth.h")
+
+STOKES, OSEEN = 0, 1
+OPS = {"K": 0, "KT": 1, "A": 2, "F": 3, "B": 4, "BT": 5, "MQ": 6, "MV": 7, "K1": 8}
+STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "EBREAKDOWN",
+          6: "EINCONSISTENT", 7: "ETIMEOUT", 8: "ENAN"}
+
+
+class EthError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("restart", ctypes.c_int),
+                ("c_stage", ctypes.c_double), ("precision", ctypes.c_int), ("mg_pre", ctypes.c_int),
+                ("mg_post", ctypes.c_int), ("mg_min_n", ctypes.c_int), ("mq_mode", ctypes.c_int),
+                ("a_exact", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("refine_inner_tol", ctypes.c_double), ("graph", ctypes.c_int), ("verbose", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters_stage1", ctypes.c_int), ("iters_stage2", ctypes.c_int),
+                ("refine_passes", ctypes.c_int), ("iters_total", ctypes.c_int),
+                ("relres_true", ctypes.c_double), ("relres0", ctypes.c_double),
+                ("prop2_lhs", ctypes.c_double), ("prop2_bound", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("alg_bytes", ctypes.c_double),
+                ("status", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Loads libeth.so (build it with ``paper_2303_10233_gb300.build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = ctypes.CDLL(path)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    pi = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "eth_sizes": (i, [i, pi, pi, pi]),
+        "eth_status_string": (ctypes.c_char_p, [i]),
+        "eth_last_error": (ctypes.c_char_p, []),
+        "eth_default_opts": (None, [ctypes.POINTER(Opts)]),
+        "eth_grid_create": (i, [i, d, d, d, d, i, vp, ctypes.POINTER(vp)]),
+        "eth_grid_destroy": (None, [vp]),
+        "eth_set_coefficients": (i, [vp, d, vp]),
+        "eth_set_rhs": (i, [vp, vp, vp]),
+        "eth_get_rhs": (i, [vp, vp]),
+        "eth_solve": (i, [vp, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]),
+        "eth_solve_host": (i, [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Stats)]),
+        "eth_solve_adjoint": (i, [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Stats)]),
+        "eth_apply": (i, [vp, i, i, vp, vp]),
+        "eth_batch_create": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
+        "eth_batch_solve": (i, [vp, ctypes.POINTER(Opts), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)]),
+        "eth_batch_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_functions(path=HEADER):
+    """Names of the functions declared in include/eth.h."""
+    src = open(path).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(eth_[a-z_0-9]+)\s*\(", src)))
+
+
+def _check(st):
+    if st != 0:
+        raise EthError(st, load().eth_last_error().decode())
+
+
+def sizes(n):
+    nv, n1, n0 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nt = load().eth_sizes(n, ctypes.byref(nv), ctypes.byref(n1), ctypes.byref(n0))
+    return nv.value, n1.value, n0.value, nt
+
+
+def make_opts(**kw):
+    o = Opts()
+    load().eth_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(f"unknown option {k}")
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": 0, "mixed": 1}[v]
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    import torch
+    if t is None:
+        return None
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Grid:
+    """Handle of one n x n Q2--Q1* problem (wraps eth_grid)."""
+
+    def __init__(self, n, kind="stokes", domain=(-1.0, 1.0, -1.0, 1.0), stream=None, device=None):
+        import torch
+        L = load()
+        self.n = int(n)
+        self.kind = OSEEN if kind in ("oseen", OSEEN) else STOKES
+        self.nv, self.n1, self.n0, self.nt = sizes(self.n)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        h = ctypes.c_void_p()
+        _check(L.eth_grid_create(self.n, *map(float, domain), self.kind,
+                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().eth_grid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _zeros(self, m):
+        import torch
+        return torch.zeros(m, dtype=torch.float64, device=self.device)
+
+    def set_coefficients(self, nu, wind=None):
+        self._wind = wind
+        _check(load().eth_set_coefficients(self.h, float(nu), _ptr(wind)))
+
+    def set_rhs(self, f_nodal, ubc):
+        _check(load().eth_set_rhs(self.h, _ptr(f_nodal), _ptr(ubc)))
+
+    def rhs(self):
+        b = self._zeros(self.nt)
+        _check(load().eth_get_rhs(self.h, _ptr(b)))
+        return b
+
+    def apply(self, op, x, fp32=False):
+        out = {"K": self.nt, "KT": self.nt, "A": 2 * self.nv, "F": 2 * self.nv, "MV": 2 * self.nv,
+               "B": self.n1 + self.n0, "BT": 2 * self.nv, "MQ": self.n1 + self.n0,
+               "K1": 2 * self.nv + self.n1}[op]
+        y = self._zeros(out)
+        _check(load().eth_apply(self.h, OPS[op], int(bool(fp32)), _ptr(x), _ptr(y)))
+        return y
+
+    def solve(self, u=None, p=None, **opts):
+        u = self._zeros(2 * self.nv) if u is None else u
+        p = self._zeros(self.n1 + self.n0) if p is None else p
+        o = make_opts(**opts)
+        st = Stats()
+        rc = load().eth_solve(self.h, ctypes.byref(o), _ptr(u), _ptr(p), ctypes.byref(st))
+        if rc not in (0, 4):
+            _check(rc)
+        return u, p, st.as_dict()
+
+    def solve_host(self, f_nodal, ubc, **opts):
+        f = np.ascontiguousarray(f_nodal, dtype=np.float64)
+        ub = np.ascontiguousarray(ubc, dtype=np.float64)
+        u = np.zeros(2 * self.nv); p = np.zeros(self.n1 + self.n0)
+        o = make_opts(**opts)
+        st = Stats()
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        rc = load().eth_solve_host(self.h, ctypes.byref(o), c(f), c(ub), c(u), c(p), ctypes.byref(st))
+        if rc not in (0, 4):
+            _check(rc)
+        return u, p, st.as_dict()
+
+    def solve_adjoint(self, ru, rp, **opts):
+        lu = self._zeros(2 * self.nv); lp = self._zeros(self.n1 + self.n0)
+        o = make_opts(**opts)
+        st = Stats()
+        rc = load().eth_solve_adjoint(self.h, ctypes.byref(o), _ptr(ru), _ptr(rp), _ptr(lu), _ptr(lp), ctypes.byref(st))
+        if rc not in (0, 4):
+            _check(rc)
+        return lu, lp, st.as_dict()
+
+
+def problem(w, device=None):
+    """Grid with coefficients and right-hand side from a workloads dict."""
+    import torch
+    g = Grid(w["n"], "oseen" if w.get("wind") is not None else "stokes", device=device)
+    dev = g.device
+    wind = None if w.get("wind") is None else torch.as_tensor(w["wind"], dtype=torch.float64, device=dev)
+    g.set_coefficients(w["nu"], wind)
+    g.set_rhs(torch.as_tensor(w["f_nodal"], dtype=torch.float64, device=dev),
+              torch.as_tensor(w["ubc"], dtype=torch.float64, device=dev))
+    return g

@@ -1,0 +1,43 @@
+"""Host-side checks of the C ABI (no GPU compute): the library builds, loads
+and exports every function that include/eth.h declares; argument validation
+rejects bad input before touching the device."""
+import ctypes
+
+import pytest
+
+from paper_2303_10233_gb300 import build as B
+from paper_2303_10233_gb300 import eth
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return eth.load()
+
+
+def test_exports_every_header_function(lib):
+    names = eth.header_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_sizes_and_defaults(lib):
+    assert eth.sizes(16) == (1089, 289, 256, 2723)
+    assert eth.sizes(256)[3] == 657923
+    assert lib.eth_sizes(0, None, None, None) == -1
+    o = eth.make_opts()
+    assert o.tol == 1e-6 and o.restart == 50 and o.c_stage == 10.0
+
+
+def test_create_rejects_bad_sizes_without_device(lib):
+    h = ctypes.c_void_p()
+    for n in (0, 1, 3, 9, 100000):
+        rc = lib.eth_grid_create(n, -1.0, 1.0, -1.0, 1.0, 0, None, ctypes.byref(h))
+        assert rc == 1 and not h.value
+    rc = lib.eth_grid_create(8, 1.0, -1.0, -1.0, 1.0, 0, None, ctypes.byref(h))
+    assert rc == 1
+    assert b"empty domain" in lib.eth_last_error()
+    assert lib.eth_set_coefficients(None, 1.0, None) == 1
+    assert lib.eth_apply(None, 0, 0, None, None) == 1
+    assert lib.eth_status_string(4) == b"not converged"

@@ -1,0 +1,82 @@
+"""Stokes solves on the GPU (MINRES + block-diagonal GMG / M_Q^+ preconditioner)
+against the FP64 oracle: exact discrete solution (bordered direct solve),
+true residual recomputed with the oracle's CSR K, element-wise conservation,
+and mesh-independent iteration counts."""
+import numpy as np
+import pytest
+
+from oracle import direct, fem, problem
+from paper_2303_10233_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eth():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_10233_gb300 import eth as E
+    return E
+
+
+def _solve(eth, w, **opts):
+    G = eth.problem(w)
+    u, p, st = G.solve(**opts)
+    x = np.concatenate([u.cpu().numpy(), p.cpu().numpy()])
+    G.close()
+    return x, st
+
+
+def _oracle(w):
+    g = fem.Grid(w["n"])
+    s = problem.System(g, w["nu"], w["wind"])
+    b = s.rhs(w["f_nodal"], w["ubc"])
+    return g, s, b
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cavity16_matches_direct(eth, precision):
+    w = W.cavity(16)
+    g, s, b = _oracle(w)
+    x, st = _solve(eth, w, tol=1e-9, precision=precision)
+    res = np.linalg.norm(b - s.K @ x) / np.linalg.norm(b)
+    assert st["status"] == 0 and res <= 1e-9 * 1.01, (st, res)
+    xd, _ = direct.solve(s, b)
+    assert np.linalg.norm(s.canonical(x) - xd) <= 1e-7 * np.linalg.norm(xd)
+    # canonical pressure returned: sum p1 = sum p0 = 0
+    assert abs(x[g.nu: g.nu + g.n1].sum()) < 1e-9 and abs(x[g.nu + g.n1:].sum()) < 1e-9
+
+
+@pytest.mark.parametrize("n", [8, 24, 64])
+def test_mms_residual_and_error(eth, n):
+    w = W.mms(n, seed=0)
+    g, s, b = _oracle(w)
+    x, st = _solve(eth, w, tol=1e-6, precision="mixed")
+    res = np.linalg.norm(b - s.K @ x) / np.linalg.norm(b)
+    assert res <= 1e-6 and abs(res - st["relres_true"]) <= 1e-3 * res + 1e-12
+    x9, st9 = _solve(eth, w, tol=1e-10, precision="mixed")
+    xd, _ = direct.solve(s, b)
+    assert np.linalg.norm(s.canonical(x9) - xd) <= 1e-5 * np.linalg.norm(xd)
+    # element-wise mass conservation of the solution: B0 u = g0
+    r0 = (s.B0I @ x9[: g.nu]) - b[g.nu + g.n1:]
+    assert np.abs(r0).max() <= 1e-8 * np.abs(b).max()
+
+
+def test_iterations_mesh_independent(eth):
+    its = []
+    for n in (16, 32, 64, 128):
+        _, st = _solve(eth, W.mms(n, seed=0), tol=1e-6, precision="fp64")
+        its.append(st["iters_total"])
+    assert max(its) - min(its) <= 10, its
+
+
+def test_zero_rhs_and_bad_options(eth):
+    w = W.cavity(8)
+    w["ubc"] = np.zeros_like(w["ubc"])
+    x, st = _solve(eth, w)
+    assert np.abs(x).max() == 0.0
+    G = eth.problem(W.cavity(8))
+    with pytest.raises(eth.EthError):
+        G.solve(tol=-1.0)
+    G.close()
