@@ -1,0 +1,339 @@
+#!/usr/bin/env python
+"""Benchmark of the enriched Taylor--Hood Stokes solve on GB300.
+
+Workload: Stokes on a 256 x 256 uniform Q2--Q1* grid of [-1,1]^2 with the
+seeded manufactured solution (six sine stream-function modes, seed 0),
+MINRES with the block-diagonal preconditioner (one GMG V(1,1) on A, M_Q^+ with
+k projected out), FP32 applies and FP64 Krylov recurrences with FP64
+iterative refinement, to a 1e-6 relative true residual.
+
+One step = one full solve to tolerance with the inputs resident in HBM.
+value = MDoF.iter/s = N_t * MINRES iterations / solve time / 1e6 (summed
+over ranks; ranks run independent replicas, no collective in the data path).
+The L2 cache (126 MB) is flushed between steps by writing a 512 MB buffer,
+outside the per-step CUDA-event timing.
+
+``--impl reference`` times the FP64 CPU oracle (SciPy, exact-block MINRES)
+on a bounded number of iterations of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_GRID = 256
+SEED = 0
+TOL = 1e-6
+METRIC = "MDoF.iter/s, Stokes 256^2 MINRES+GMG to 1e-6 rel. residual"
+UNIT = "MDoF.iter/s"
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0])); smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) sample: exact-block MINRES iterations on the same workload
+# ---------------------------------------------------------------------------
+def oracle_sample(n, iters, setup=None):
+    import numpy as np
+    from oracle import fem, krylov, problem
+    from paper_2303_10233_gb300 import workloads as W
+    if setup is None:
+        w = W.mms(n, seed=SEED)
+        g = fem.Grid(n)
+        s = problem.System(g, w["nu"], w["wind"])
+        b = s.rhs(w["f_nodal"], w["ubc"])
+        t = time.perf_counter()
+        P = krylov.P1(s)
+        tfac = time.perf_counter() - t
+        setup = (g, s, b, P, tfac)
+    g, s, b, P, tfac = setup
+    x0 = np.concatenate([s.DB @ b[: g.nu], np.zeros(g.np_)])
+    t = time.perf_counter()
+    x, info = krylov.minres(lambda v: s.K @ v, P, b, x0, tol=1e-30, maxit=iters)
+    dt = time.perf_counter() - t
+    return info["its"], dt, setup
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2303_10233_gb300 import workloads as W
+    nt = W.sizes(N_GRID)[4]
+    its, dt, setup = oracle_sample(N_GRID, 2)          # includes the factorisation of the exact blocks
+    per_it = dt / max(its, 1)
+    budget = 150.0 / max(args.steps + args.warmup, 1)
+    m = max(2, min(40, int(budget / max(per_it, 1e-3))))
+    for _ in range(args.warmup):
+        oracle_sample(N_GRID, m, setup)
+    vals, times = [], []
+    for _ in range(args.steps):
+        its, dt, _ = oracle_sample(N_GRID, m, setup)
+        vals.append(nt * its / dt / 1e6)
+        times.append(dt)
+    value = nt * m * len(times) / sum(times) / 1e6
+    sample = (f"{m} MINRES iterations (Algorithm 1, exact P_1 blocks by SuperLU, factorised once in "
+              f"{setup[4]:.1f} s, not timed) per step on the 256^2 MMS system, N_t={nt}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "stokes_mms_256", "n": N_GRID, "N_t": nt},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_10233_gb300 import eth, workloads as W
+
+    w = W.mms(N_GRID, seed=SEED)
+    G = eth.problem(w, device=local)
+    nt = G.nt
+    opts = dict(tol=TOL, precision="mixed")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        G.solve(**opts)
+    torch.cuda.synchronize()
+
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stats = []
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1 = evs[k]
+        e0.record()
+        _, _, st = G.solve(**opts)
+        e1.record()
+        stats.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    t_wall = time.perf_counter() - t_wall
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    its = sum(s["iters_total"] for s in stats)
+    tot_s = sum(step_ms) / 1e3
+    if dist:
+        tt = torch.tensor([tot_s, its], dtype=torch.float64, device="cuda")
+        mx = tt.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = tt.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        tot_max, its_all = float(mx[0]), float(sm[1])
+    else:
+        tot_max, its_all = tot_s, its
+    value = nt * its_all / tot_max / 1e6
+    launches = sum(s["kernel_launches"] for s in stats)
+
+    # ---- plain FP64 GPU form (same solve, FP64 applies and FP64 multigrid)
+    G.solve(tol=TOL, precision="fp64")
+    f64_ms = []
+    f64_its = 0
+    for k in range(min(5, args.steps)):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, _, st = G.solve(tol=TOL, precision="fp64")
+        e1.record()
+        torch.cuda.synchronize()
+        f64_ms.append(e0.elapsed_time(e1))
+        f64_its += st["iters_total"]
+
+    # ---- end to end through the C ABI with pinned host buffers
+    nu2 = 2 * G.nv
+    fh = torch.from_numpy(np.ascontiguousarray(w["f_nodal"])).pin_memory()
+    uh = torch.from_numpy(np.ascontiguousarray(w["ubc"])).pin_memory()
+    uo = torch.empty(nu2, dtype=torch.float64).pin_memory()
+    po = torch.empty(G.n1 + G.n0, dtype=torch.float64).pin_memory()
+    G.solve_host_pinned(fh, uh, uo, po, **opts)
+    torch.cuda.synchronize()
+    e2e_its = 0
+    e2e_t = 0.0
+    for k in range(min(10, args.steps)):
+        flush.fill_(float(k))
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st = G.solve_host_pinned(fh, uh, uo, po, **opts)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_t += e0.elapsed_time(e1) / 1e3
+        e2e_its += st["iters_total"]
+    e2e_value = nt * e2e_its / e2e_t / 1e6 * ws
+    h2d = 2 * nu2 * 8
+    d2h = nt * 8
+
+    # ---- roofline of the dominant kernel, timed live on the launching stream
+    roof = roofline(G, torch, eth)
+    clocks = clk.stop()
+
+    if rank != 0:
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu:
+        its_c, dt_c, setup = oracle_sample(N_GRID, 2)
+        m = max(2, min(30, int(15.0 / max(dt_c / max(its_c, 1), 1e-3))))
+        its_c, dt_c, _ = oracle_sample(N_GRID, m, setup)
+        cpu = {"value": nt * its_c / dt_c / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{its_c} exact-block MINRES iterations of the 256^2 MMS system in {dt_c:.1f} s "
+                         f"(SuperLU factorisation {setup[4]:.1f} s excluded); SciPy sparse, single-threaded"}
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 applies / f64 Krylov", "data": "synthetic",
+        "config": {"workload": "stokes_mms_256", "n": N_GRID, "N_t": nt, "tol": TOL, "precision": "mixed",
+                   "preconditioner": "blkdiag(GMG V(1,1) Jacobi, M_Q^+ via Q1 V-cycle)",
+                   "l2": "512 MB buffer written between steps (outside per-step events)",
+                   "parallelism": f"replicas x{ws}"},
+        "time_to_tol_ms": statistics.median(step_ms),
+        "iters_per_solve": its / max(len(stats), 1),
+        "relres": max(s["relres_true"] for s in stats),
+        "fp64_plain": {"ms": statistics.median(f64_ms) if f64_ms else None,
+                       "iters_per_solve": f64_its / max(len(f64_ms), 1),
+                       "speedup_mixed_vs_fp64": (statistics.median(f64_ms) / statistics.median(step_ms)) if f64_ms else None},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+        "wall_s": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    G.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def roofline(G, torch, eth):
+    """Fused K apply (FP32 element arithmetic, FP64 in/out) on the 512^2 grid
+    of the same workload family: algorithmic bytes = 16 B x N_t per launch."""
+    from paper_2303_10233_gb300 import workloads as W
+    peak, src = _peaks()
+    n = 512
+    w = W.mms(n, seed=SEED)
+    H = eth.problem(w, device=G.device.index)
+    x = torch.randn(H.nt, dtype=torch.float64, device=G.device)
+    y = torch.empty_like(x)
+    for _ in range(3):
+        eth.load().eth_apply(H.h, eth.OPS["K"], 1, eth._ptr(x), eth._ptr(y))
+    torch.cuda.synchronize()
+    reps = 50
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        eth.load().eth_apply(H.h, eth.OPS["K"], 1, eth._ptr(x), eth._ptr(y))
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / reps / 1e3
+    bytes_ = 16.0 * H.nt
+    ach = bytes_ / t / 1e9
+    H.close()
+    return {"kernel": "k_q2 fused K apply (FP32 math, FP64 I/O), n=512", "bound": "hbm", "achieved": ach,
+            "peak": peak, "unit": "GB/s", "frac": ach / peak, "peak_source": src, "traffic": None,
+            "alg_bytes_per_launch": bytes_, "us_per_launch": t * 1e6}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

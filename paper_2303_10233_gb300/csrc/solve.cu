@@ -23,6 +23,7 @@ struct Work {
   cudaEvent_t evf = nullptr, evj = nullptr, evu = nullptr, t0 = nullptr, t1 = nullptr;
   cudaGraphExec_t gexec = nullptr;
   int gkey = -1;
+  long glaunch = 0;            // kernels in one replay of gexec
   int nmin_built = -1;
 };
 
@@ -335,6 +336,7 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
   const double area = g->hx * g->hy;
   k_init_scalars<<<1, 1, 0, g->s>>>(g->sc, tol, (double)g->n1, (double)g->n0, 16.0 / area, g->nu);
   ETH_CUDA(cudaGetLastError());
+  g->launches++;
   ETH_CUDA(cudaMemsetAsync(w->d, 0, nt * 8, g->s));
   ETH_CUDA(cudaMemsetAsync(w->W[0], 0, nt * 8, g->s));
   ETH_CUDA(cudaMemsetAsync(w->W[1], 0, nt * 8, g->s));
@@ -346,6 +348,7 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
     Slot s = slot_of(g, SL_VSUM, nb, FIN_VSUMS);
     k_psums<<<nb, 256, 0, g->s>>>(2 * (size_t)g->nv, (size_t)g->n1, (size_t)g->n0, w->V[1], s);
     ETH_CUDA(cudaGetLastError());
+    g->launches++;
   }
   ETH_TRY(precond_stokes<T>(g, w, o, w->V[1], w->Z[1], FIN_MINRES_INIT, nullptr));
   ETH_TRY(read_scalars(g));
@@ -358,10 +361,13 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
       if (!w->gexec || w->gkey != key) {
         if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; }
         cudaGraph_t graph;
+        const long l0 = g->launches;
         ETH_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
         eth_status st = minres_iter<T>(g, w, o, fp32, 1);
         if (st == ETH_OK) st = minres_iter<T>(g, w, o, fp32, 2);
         cudaError_t ce = cudaStreamEndCapture(g->s, &graph);
+        w->glaunch = g->launches - l0;
+        g->launches = l0;
         if (st != ETH_OK) return st;
         ETH_CUDA(ce);
         ETH_CUDA(cudaGraphInstantiate(&w->gexec, graph, 0));
@@ -369,6 +375,7 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
         w->gkey = key;
       }
       ETH_CUDA(cudaGraphLaunch(w->gexec, g->s));
+      g->launches += w->glaunch;
     } else {
       ETH_TRY(minres_iter<T>(g, w, o, fp32, j));
       ETH_TRY(minres_iter<T>(g, w, o, fp32, j + 1));
@@ -436,6 +443,7 @@ static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stat
     ETH_CUDA(cudaMemsetAsync(w->Kz, 0, nt * 8, g->s));
     k_residual<<<nb, 256, 0, g->s>>>(nt, w->bp, w->Kz, w->r, slot_of(g, SL_NORM, nb, FIN_STORE));
     ETH_CUDA(cudaGetLastError());
+    g->launches++;
     ETH_CUDA(cudaMemcpyAsync(&g->sch->dots[SL_NORM], &g->sc->dots[SL_NORM], 8, cudaMemcpyDeviceToHost, g->s));
     ETH_CUDA(cudaStreamSynchronize(g->s));
     bb = g->sch->dots[SL_NORM];
@@ -468,6 +476,7 @@ static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stat
     const int nb = vblocks(nt);
     k_add<<<nb, 256, 0, g->s>>>(nt, w->x, w->d);
     ETH_CUDA(cudaGetLastError());
+    g->launches++;
     ETH_TRY(canonicalize(g, w->x));
     ETH_TRY(true_residual(g, w, w->bp, &rr));
     rel = std::sqrt(rr) / nb2;
@@ -529,6 +538,7 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   ETH_CUDA(cudaMemcpyAsync(w->x + nu2, p, (size_t)(g->n1 + g->n0) * 8, cudaMemcpyDeviceToDevice, g->s));
   k_set_boundary<<<vblocks(nu2), 256, 0, g->s>>>(g->n, w->x, g->ubc);
   ETH_CUDA(cudaGetLastError());
+  g->launches++;
   eth_status r = o.precision == ETH_MIXED ? stokes_solve<float>(g, w, &o, &st) : stokes_solve<double>(g, w, &o, &st);
   if (r == ETH_ECUDA || r == ETH_ENOMEM || r == ETH_EINVAL) return r;
   ETH_CUDA(cudaMemcpyAsync(u, w->x, nu2 * 8, cudaMemcpyDeviceToDevice, g->s));

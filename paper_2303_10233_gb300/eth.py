@@ -200,6 +200,17 @@ class Grid:
             _check(rc)
         return u, p, st.as_dict()
 
+    def solve_host_pinned(self, f_pinned, ubc_pinned, u_pinned, p_pinned, **opts):
+        """eth_solve_host with caller-owned (pinned) host tensors; returns stats."""
+        o = make_opts(**opts)
+        st = Stats()
+        c = lambda t: ctypes.c_void_p(t.data_ptr())
+        rc = load().eth_solve_host(self.h, ctypes.byref(o), c(f_pinned), c(ubc_pinned), c(u_pinned),
+                                   c(p_pinned), ctypes.byref(st))
+        if rc not in (0, 4):
+            _check(rc)
+        return st.as_dict()
+
     def solve_adjoint(self, ru, rp, **opts):
         lu = self._zeros(2 * self.nv); lp = self._zeros(self.n1 + self.n0)
         o = make_opts(**opts)
