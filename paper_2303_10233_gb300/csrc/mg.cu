@@ -490,8 +490,8 @@ eth_status mg_build_q1(eth_grid* g, Hier<T>& H, int nmin) {
 // V-cycles
 // ---------------------------------------------------------------------------
 template <class T, class TO, int EPI, int CF>
-static eth_status q2_level(eth_grid* g, const Level<T>& L, const T* x, TO* y, T omega, const double* bsrc,
-                           const int* done, const Slot* slot, int slot_off, const double* dv) {
+static eth_status q2_level(eth_grid* g, const Level<T>& L, const T* x, TO* y, T omega, const TO* bsrc,
+                           const int* done, const Slot* slot, int slot_off, const TO* dv) {
   constexpr int F0 = QF_DIFF | QF_XIN | QF_UOUT | CF;
   Q2Params<T, TO, T> P{};
   P.n = L.n; P.hx = (T)L.hx; P.hy = (T)L.hy; P.nu = (T)L.nu; P.sd = (T)L.sd;
@@ -507,8 +507,8 @@ static eth_status q2_level(eth_grid* g, const Level<T>& L, const T* x, TO* y, T 
 }
 
 template <class T, class TO, int EPI>
-static eth_status q2_level_d(eth_grid* g, const Level<T>& L, const T* x, TO* y, T omega, const double* bsrc,
-                             const int* done, const Slot* slot = nullptr, int slot_off = 0, const double* dv = nullptr) {
+static eth_status q2_level_d(eth_grid* g, const Level<T>& L, const T* x, TO* y, T omega, const TO* bsrc,
+                             const int* done, const Slot* slot = nullptr, int slot_off = 0, const TO* dv = nullptr) {
   if (L.w != nullptr && L.sd > 0.0) return q2_level<T, TO, EPI, QF_CONV | QF_SD>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
   if (L.w != nullptr) return q2_level<T, TO, EPI, QF_CONV>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
   return q2_level<T, TO, EPI, 0>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);

@@ -38,7 +38,9 @@ enum : int {
   QF_NOBC = 1024,   // no Dirichlet masking / identity rows
   QF_SD = 2048,     // streamline diffusion sum_T d_T int (w.grad u)(w.grad v) (coarse levels)
 };
-enum : int { EPI_APPLY = 0, EPI_SMOOTH = 1, EPI_RESID = 2 };
+enum : int { EPI_APPLY = 0, EPI_SMOOTH = 1, EPI_RESID = 2, EPI_SCALE = 3, EPI_BSUB = 4 };
+// EPI_SCALE: y = dinv * (op x) on the interior, 0 on the boundary.
+// EPI_BSUB:  y = bsrc - (op x) on the interior, bsrc on the boundary.
 
 template <class TI, class TO, class CT>
 struct Q2Params {
@@ -55,9 +57,9 @@ struct Q2Params {
   CT sd;            // QF_SD coefficient c: d_T = c h / (2|w|_T) (1 - 1/Pe_T) when Pe_T > 1
   Slot slot;        // QF_DOT
   int slot_off;
-  const double* dv;   // QF_DOT partner of the velocity output (FP64)
-  const double* dvp;  // QF_DOT partner of the pressure output (FP64)
-  const double* bsrc; // EPI_SMOOTH / EPI_RESID: boundary rows copy bsrc (else 0)
+  const TO* dv;       // QF_DOT partner of the velocity output
+  const TO* dvp;      // QF_DOT partner of the pressure output
+  const TO* bsrc;     // EPI_SMOOTH: boundary rows copy bsrc (else 0); EPI_BSUB: minuend
   const int* done;    // optional early-exit flag
 };
 
@@ -316,8 +318,12 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
           o0 = (TO)(sx[s] + di * (P.b[g] - s0));
           o1 = (TO)(sx[SQY * SQX + s] + di * (P.b[g + nv] - s1));
         }
-      } else {  // EPI_RESID
+      } else if (EPI == EPI_RESID) {
         if (bnd) { o0 = 0; o1 = 0; } else { o0 = (TO)(P.b[g] - s0); o1 = (TO)(P.b[g + nv] - s1); }
+      } else if (EPI == EPI_SCALE) {
+        if (bnd) { o0 = 0; o1 = 0; } else { o0 = (TO)(P.dinv[g] * s0); o1 = (TO)(P.dinv[g] * s1); }
+      } else {  // EPI_BSUB
+        if (bnd) { o0 = P.bsrc[g]; o1 = P.bsrc[g + nv]; } else { o0 = P.bsrc[g] - (TO)s0; o1 = P.bsrc[g + nv] - (TO)s1; }
       }
       P.y[g] = o0;
       P.y[g + nv] = o1;

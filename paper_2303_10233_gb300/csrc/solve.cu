@@ -11,25 +11,10 @@
 
 namespace eth {
 
-enum : int { SL_DELTA = 0, SL_VSUM = 1, SL_GAMMA = 2, SL_MQ = 3, SL_DONE = 4, SL_NORM = 5, SL_PSUM = 6, SL_GEN = 7 };
-
-struct Work {
-  Hier<float> vf, qf;
-  Hier<double> vd, qd;
-  double *x = nullptr, *d = nullptr, *r = nullptr, *Kz = nullptr, *bp = nullptr;
-  double *V[2] = {nullptr, nullptr}, *Z[2] = {nullptr, nullptr}, *W[2] = {nullptr, nullptr};
-  cudaStream_t s2 = nullptr;   // second branch (pressure block)
-  cudaStream_t sm = nullptr;   // internal main stream (capturable), joined to the user stream
-  cudaEvent_t evf = nullptr, evj = nullptr, evu = nullptr, t0 = nullptr, t1 = nullptr;
-  cudaGraphExec_t gexec = nullptr;
-  int gkey = -1;
-  long glaunch = 0;            // kernels in one replay of gexec
-  int nmin_built = -1;
-};
-
 static void work_free(void* p) {
   Work* w = (Work*)p;
   if (!w) return;
+  gmres_free(w);
   mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
   cudaFree(w->x); cudaFree(w->d); cudaFree(w->r); cudaFree(w->Kz); cudaFree(w->bp);
   for (int k = 0; k < 2; ++k) { cudaFree(w->V[k]); cudaFree(w->Z[k]); cudaFree(w->W[k]); }
@@ -54,10 +39,11 @@ eth_status solver_coefficients_changed(eth_grid* g) {
   if (!w) return ETH_OK;
   mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
   if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; w->gkey = -1; }
+  gmres_free(w);
   return ETH_OK;
 }
 
-static eth_status work_get(eth_grid* g, Work** out) {
+eth_status work_get(eth_grid* g, Work** out) {
   if (g->ws) { *out = (Work*)g->ws; return ETH_OK; }
   Work* w = new Work();
   g->ws = w;
@@ -76,13 +62,13 @@ static eth_status work_get(eth_grid* g, Work** out) {
   return ETH_OK;
 }
 
-static int vblocks(size_t m) {
+int vblocks(size_t m) {
   size_t b = (m + 255) / 256;
   if (b > 152 * 8) b = 152 * 8;
   return (int)(b < 1 ? 1 : b);
 }
 
-static Slot slot_of(eth_grid* g, int which, int total, int op) {
+Slot slot_of(eth_grid* g, int which, int total, int op) {
   Slot s = make_slot(g, which, total);
   s.op = op;
   return s;
@@ -100,16 +86,6 @@ __global__ void k_residual(size_t m, const double* __restrict__ b, const double*
   }
   double v[1] = {acc};
   if (slot_arrive<1>(sl, blockIdx.x, v)) finish_slot(sl, v[0]);
-}
-
-// sums of the Q1 and P0 pressure blocks of x (length nt): FIN_STORE of (sum p1, sum p0)
-__global__ void k_psums(size_t off, size_t n1, size_t n0, const double* __restrict__ x, Slot sl) {
-  double a1 = 0.0, a0 = 0.0;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1 + n0; k += (size_t)gridDim.x * blockDim.x) {
-    if (k < n1) a1 += x[off + k]; else a0 += x[off + k];
-  }
-  double v[2] = {a1, a0};
-  if (slot_arrive<2>(sl, blockIdx.x, v)) finish_slot_n<2>(sl, v);
 }
 
 // x_p1 -= sum_p1 / n1 ; x_p0 -= sum_p0 / n0  (sums in sums[0], sums[1])
@@ -249,11 +225,11 @@ __global__ void k_mq_out(int n, const T* __restrict__ zt, const double* __restri
   if (slot_arrive<1>(gsl, goff + blockIdx.x, v)) finish_slot(gsl, v[0]);
 }
 
-static int mq_blocks(eth_grid* g) { return vblocks((size_t)g->n1 + g->n0); }
+int mq_blocks(eth_grid* g) { return vblocks((size_t)g->n1 + g->n0); }
 
 template <class T>
-static eth_status precond_pressure(eth_grid* g, Hier<T>& Q, const double* vp, double* zp, const Slot& gsl, int goff,
-                                   const int* done, cudaStream_t s) {
+eth_status precond_pressure(eth_grid* g, Hier<T>& Q, const double* vp, double* zp, const Slot& gsl, int goff,
+                            const int* done, cudaStream_t s) {
   Level<T>& L0 = Q.lv[0];
   const cudaStream_t keep = g->s;
   g->s = s;
@@ -272,18 +248,16 @@ static eth_status precond_pressure(eth_grid* g, Hier<T>& Q, const double* vp, do
   return ETH_OK;
 }
 
-template <class T>
-static Hier<T>& vel_hier(Work* w);
 template <>
 Hier<float>& vel_hier<float>(Work* w) { return w->vf; }
 template <>
 Hier<double>& vel_hier<double>(Work* w) { return w->vd; }
-template <class T>
-static Hier<T>& q1_hier(Work* w);
 template <>
 Hier<float>& q1_hier<float>(Work* w) { return w->qf; }
 template <>
 Hier<double>& q1_hier<double>(Work* w) { return w->qd; }
+template eth_status precond_pressure<float>(eth_grid*, Hier<float>&, const double*, double*, const Slot&, int, const int*, cudaStream_t);
+template eth_status precond_pressure<double>(eth_grid*, Hier<double>&, const double*, double*, const Slot&, int, const int*, cudaStream_t);
 
 // z = P^{-1} v with the fused <z, v> into the gamma slot (finisher fin).
 // The velocity V-cycle and the pressure block run on two streams (fork/join).
@@ -323,7 +297,7 @@ static eth_status minres_iter(eth_grid* g, Work* w, const eth_opts* o, bool fp32
   return ETH_OK;
 }
 
-static eth_status read_scalars(eth_grid* g) {
+eth_status read_scalars(eth_grid* g) {
   ETH_CUDA(cudaMemcpyAsync(g->sch, g->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->s));
   ETH_CUDA(cudaStreamSynchronize(g->s));
   return ETH_OK;
@@ -346,7 +320,7 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
   {
     const int nb = vblocks((size_t)g->n1 + g->n0);
     Slot s = slot_of(g, SL_VSUM, nb, FIN_VSUMS);
-    k_psums<<<nb, 256, 0, g->s>>>(2 * (size_t)g->nv, (size_t)g->n1, (size_t)g->n0, w->V[1], s);
+    k_psums<0><<<nb, 256, 0, g->s>>>(2 * (size_t)g->nv, (size_t)g->n1, (size_t)g->n0, w->V[1], s);
     ETH_CUDA(cudaGetLastError());
     g->launches++;
   }
@@ -390,7 +364,7 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
 }
 
 template <class T>
-static eth_status ensure_hier(eth_grid* g, Work* w, const eth_opts* o) {
+eth_status ensure_hier(eth_grid* g, Work* w, const eth_opts* o) {
   const int nmin = std::max(2, o->mg_min_n);
   if (w->nmin_built != nmin) {
     mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
@@ -405,7 +379,7 @@ static eth_status ensure_hier(eth_grid* g, Work* w, const eth_opts* o) {
 }
 
 // ||b - K x||^2 in FP64 (K applied with FP64 element arithmetic); result to host.
-static eth_status true_residual(eth_grid* g, Work* w, const double* b, double* rr) {
+eth_status true_residual(eth_grid* g, Work* w, const double* b, double* rr) {
   ETH_TRY(op_apply_K(g, false, false, w->x, w->Kz, nullptr));
   const int nb = vblocks(g->nt);
   k_residual<<<nb, 256, 0, g->s>>>((size_t)g->nt, b, w->Kz, w->r, slot_of(g, SL_NORM, nb, FIN_STORE));
@@ -418,10 +392,10 @@ static eth_status true_residual(eth_grid* g, Work* w, const double* b, double* r
 }
 
 // remove the e1 / e0 components of the pressure block of x (Euclidean)
-static eth_status canonicalize(eth_grid* g, double* x) {
+eth_status canonicalize(eth_grid* g, double* x) {
   const int nb = vblocks((size_t)g->n1 + g->n0);
   const size_t off = 2 * (size_t)g->nv;
-  k_psums<<<nb, 256, 0, g->s>>>(off, (size_t)g->n1, (size_t)g->n0, x, slot_of(g, SL_PSUM, nb, FIN_STORE));
+  k_psums<0><<<nb, 256, 0, g->s>>>(off, (size_t)g->n1, (size_t)g->n0, x, slot_of(g, SL_PSUM, nb, FIN_STORE));
   ETH_CUDA(cudaGetLastError());
   k_psub<<<nb, 256, 0, g->s>>>(off, (size_t)g->n1, (size_t)g->n0, x, &g->sc->dots[SL_PSUM]);
   ETH_CUDA(cudaGetLastError());
@@ -492,24 +466,8 @@ static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stat
   return result;
 }
 
-// Runs the solver body on the handle's internal stream (capturable even when
-// the user stream is the legacy default stream), ordered after and before the
-// user stream's work.
-struct StreamSwap {
-  eth_grid* g;
-  Work* w;
-  cudaStream_t user;
-  StreamSwap(eth_grid* g_, Work* w_) : g(g_), w(w_), user(g_->s) {
-    cudaEventRecord(w->evu, user);
-    cudaStreamWaitEvent(w->sm, w->evu, 0);
-    g->s = w->sm;
-  }
-  ~StreamSwap() {
-    cudaEventRecord(w->evu, w->sm);
-    cudaStreamWaitEvent(user, w->evu, 0);
-    g->s = user;
-  }
-};
+template eth_status ensure_hier<float>(eth_grid*, Work*, const eth_opts*);
+template eth_status ensure_hier<double>(eth_grid*, Work*, const eth_opts*);
 
 }  // namespace eth
 
@@ -524,7 +482,6 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   if (opts) o = *opts; else eth_default_opts(&o);
   if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1) { set_error("eth_solve: bad options"); return ETH_EINVAL; }
   if (o.precision != ETH_FP64 && o.precision != ETH_MIXED) { set_error("eth_solve: bad precision"); return ETH_EINVAL; }
-  if (g->kind != ETH_STOKES) { set_error("eth_solve: Oseen solver not available in this build"); return ETH_EINVAL; }
   eth_stats st;
   std::memset(&st, 0, sizeof(st));
   Work* w;
@@ -539,7 +496,9 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   k_set_boundary<<<vblocks(nu2), 256, 0, g->s>>>(g->n, w->x, g->ubc);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
-  eth_status r = o.precision == ETH_MIXED ? stokes_solve<float>(g, w, &o, &st) : stokes_solve<double>(g, w, &o, &st);
+  eth_status r;
+  if (g->kind == ETH_OSEEN) r = oseen_solve(g, w, &o, &st, false);
+  else r = o.precision == ETH_MIXED ? stokes_solve<float>(g, w, &o, &st) : stokes_solve<double>(g, w, &o, &st);
   if (r == ETH_ECUDA || r == ETH_ENOMEM || r == ETH_EINVAL) return r;
   ETH_CUDA(cudaMemcpyAsync(u, w->x, nu2 * 8, cudaMemcpyDeviceToDevice, g->s));
   ETH_CUDA(cudaMemcpyAsync(p, w->x + nu2, (size_t)(g->n1 + g->n0) * 8, cudaMemcpyDeviceToDevice, g->s));

@@ -1,0 +1,44 @@
+"""Oseen solves on the GPU (two-stage PCD GMRES, Sec. 3.1) against the FP64
+oracle: exact discrete solution, true residual with the oracle's CSR K, the
+Prop. 2 bound at the stage switch, and FP64 vs mixed precision."""
+import numpy as np
+import pytest
+
+from oracle import direct, fem, problem
+from paper_2303_10233_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eth():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_10233_gb300 import eth as E
+    return E
+
+
+def _run(eth, w, **opts):
+    G = eth.problem(w)
+    u, p, st = G.solve(**opts)
+    x = np.concatenate([u.cpu().numpy(), p.cpu().numpy()])
+    G.close()
+    return x, st
+
+
+@pytest.mark.parametrize("n,nu", [(16, 1 / 100), (32, 1 / 100), (64, 1 / 50)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_oseen_matches_direct(eth, n, nu, precision):
+    w = W.oseen_cavity(n, nu=nu, seed=1)
+    g = fem.Grid(n)
+    s = problem.System(g, w["nu"], w["wind"])
+    b = s.rhs(w["f_nodal"], w["ubc"])
+    x, st = _run(eth, w, tol=1e-9, precision=precision, mg_min_n=8)
+    res = np.linalg.norm(b - s.K @ x) / np.linalg.norm(b)
+    assert st["status"] == 0 and res <= 1e-9 * 1.01, (st, res)
+    xd, _ = direct.solve(s, b)
+    assert np.linalg.norm(s.canonical(x) - xd) <= 1e-6 * np.linalg.norm(xd)
+    assert st["iters_stage1"] > 0 and st["iters_stage2"] >= 0
+    # Prop. 2 at the switch: ||z*||^2 <= c^2 eta^2 ||f||^2 + ||r0*||^2
+    assert st["prop2_lhs"] <= st["prop2_bound"] * (1 + 1e-6)
