@@ -321,6 +321,22 @@ def roofline(G, torch, eth):
             "alg_bytes_per_launch": bytes_, "us_per_launch": t * 1e6}
 
 
+def profile_apply(n, kind):
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_10233_gb300 import eth, workloads as W
+    w = W.oseen_cavity(n, nu=0.01, seed=1) if kind == "oseen" else W.mms(n, seed=SEED)
+    G = eth.problem(w)
+    x = torch.randn(G.nt, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(5):
+        eth.load().eth_apply(G.h, eth.OPS["K"], 1, eth._ptr(x), eth._ptr(y))
+    torch.cuda.synchronize()
+    print(f"profile_apply n={n} kind={kind} N_t={G.nt} done")
+    G.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -328,7 +344,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--profile-apply", type=int, default=0, metavar="N",
+                    help="only run the fused K apply (FP32 math) 5 times on an N x N grid (for ncu captures)")
+    ap.add_argument("--profile-kind", default="stokes", choices=["stokes", "oseen"])
     args = ap.parse_args()
+    if args.profile_apply:
+        profile_apply(args.profile_apply, args.profile_kind)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -60,10 +60,11 @@ typedef enum { ETH_STOKES = 0, ETH_OSEEN = 1 } eth_kind;
  * KT: its transpose (element-transposed convection); A: nu*A (Dirichlet);
  * F: nu*A + N(w) (Dirichlet); B: [B1;B0] D_I u; BT: D_I B^T p;
  * MQ: M_Q = [Qk R^T; R Q0] (Sec. 2.3); MV: per-component Q2 mass (no BC);
- * K1: reduced system [F B1^T; B1 0] on [u; p1] (Sec. 3.1 Eq. reduced-system). */
+ * K1: reduced system [F B1^T; B1 0] on [u; p1] (Sec. 3.1 Eq. reduced-system);
+ * K1T: its transpose [F^T B1^T; B1 0]. */
 typedef enum {
   ETH_OP_K = 0, ETH_OP_KT = 1, ETH_OP_A = 2, ETH_OP_F = 3, ETH_OP_B = 4,
-  ETH_OP_BT = 5, ETH_OP_MQ = 6, ETH_OP_MV = 7, ETH_OP_K1 = 8
+  ETH_OP_BT = 5, ETH_OP_MQ = 6, ETH_OP_MV = 7, ETH_OP_K1 = 8, ETH_OP_K1T = 9
 } eth_op;
 
 /* Precision of the internal arithmetic. */
@@ -151,8 +152,18 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
 /* y = op(x) for one operator (see eth_op); fp32 != 0 selects FP32 element
  * arithmetic (inputs and outputs stay FP64).  Sizes: K, KT: N_t -> N_t;
  * A, F, MV: 2 N_v -> 2 N_v; B: 2 N_v -> N_1+N_0; BT: N_1+N_0 -> 2 N_v;
- * MQ: N_1+N_0 -> N_1+N_0; K1: 2 N_v+N_1 -> 2 N_v+N_1. */
+ * MQ: N_1+N_0 -> N_1+N_0; K1, K1T: 2 N_v+N_1 -> 2 N_v+N_1. */
 eth_status eth_apply(eth_grid* g, eth_op op, int fp32, const double* x_dev, double* y_dev);
+
+/* Gradients of J(u) = ||u - u_t||^2 from the adjoint velocity l_u (device,
+ * 2 N_v; the solution of eth_solve_adjoint with r_u = 2(u - u_t), r_p = 0)
+ * and the state velocity u (device, 2 N_v, boundary values included):
+ *   grad_f  = M_v D_I l_u      (device, 2 N_v; d J / d f_nodal, f entering as M_v f)
+ *   grad_nu = -(D_I l_u)^T A u (host scalar; d J / d nu, A the unscaled Laplacian)
+ * D_I zeroes the Dirichlet nodes.  No counterpart in the paper: the
+ * differentiation form wraps the solver (adjoint of K(nu) x = b(f, nu)). */
+eth_status eth_adjoint_gradients(eth_grid* g, const double* lu_dev, const double* u_dev,
+                                 double* grad_f_dev, double* grad_nu_host);
 
 /* Batched solves of independent instances (each created with its own handle,
  * all on the same stream). */

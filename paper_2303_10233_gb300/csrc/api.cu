@@ -163,7 +163,7 @@ eth_status eth_apply(eth_grid* g, eth_op op, int fp32, const double* x, double* 
     set_error("eth_apply: call eth_set_coefficients first");
     return ETH_EINVAL;
   }
-  if ((int)op < 0 || (int)op > (int)ETH_OP_K1) { set_error("eth_apply: bad operator %d", (int)op); return ETH_EINVAL; }
+  if ((int)op < 0 || (int)op > (int)ETH_OP_K1T) { set_error("eth_apply: bad operator %d", (int)op); return ETH_EINVAL; }
   return op_apply(g, op, fp32 != 0, x, y);
 }
 

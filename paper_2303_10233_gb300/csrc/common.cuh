@@ -36,6 +36,51 @@ __host__ __device__ constexpr double q1d(int c) { return c == 0 ? -1.0 : 1.0; }
 #define GW(q) ((CT)::eth::gw(q))
 
 // ---------------------------------------------------------------------------
+// FP64 <-> FP32 conversions by integer operations on the IEEE-754 bit fields.
+// On GB300 the hardware conversion instruction runs at the (reduced) FP64
+// rate, which makes it the bottleneck of an FP32 element kernel with FP64
+// inputs and outputs; the integer ALUs are not limited that way.
+// binary64 -> binary32: rebias the exponent (1023 -> 127), keep the top 23
+// mantissa bits and round half up on the first discarded bit (error <= 1/2
+// ulp; the carry propagates into the exponent, overflowing to infinity).
+// Magnitudes below the smallest normal binary32 become signed zero.
+// binary32 -> binary64 is exact for normal numbers (subnormals become zero).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float f64_to_f32_bits(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const unsigned sign = hi & 0x80000000u;
+  const unsigned e64 = (hi >> 20) & 0x7ffu;
+  const int e = (int)e64 - 896;
+  const unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+  unsigned bits;
+  if (e64 == 0x7ffu) bits = sign | 0x7f800000u | (((hi & 0xfffffu) | lo) ? 0x400000u : 0u);
+  else if (e <= 0) bits = sign;
+  else if (e >= 255) bits = sign | 0x7f800000u;
+  else bits = (sign | ((unsigned)e << 23) | m) + ((lo >> 28) & 1u);
+  return __uint_as_float(bits);
+}
+
+__device__ __forceinline__ double f32_to_f64_bits(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned sign = b & 0x80000000u;
+  const unsigned e = (b >> 23) & 0xffu;
+  const unsigned m = b & 0x7fffffu;
+  unsigned hi, lo;
+  if (e == 0u) { hi = sign; lo = 0u; }
+  else if (e == 255u) { hi = sign | 0x7ff00000u | (m >> 3); lo = m << 29; }
+  else { hi = sign | ((e + 896u) << 20) | (m >> 3); lo = m << 29; }
+  return __hiloint2double((int)hi, (int)lo);
+}
+
+template <class TO, class TI>
+__device__ __forceinline__ TO cvt(TI v) { return (TO)v; }
+template <>
+__device__ __forceinline__ float cvt<float, double>(double v) { return f64_to_f32_bits(v); }
+template <>
+__device__ __forceinline__ double cvt<double, float>(float v) { return f32_to_f64_bits(v); }
+
+// ---------------------------------------------------------------------------
 // Grid-wide deterministic reductions: every block writes one partial, the
 // last block to arrive (ticket counter) sums the partials in block order and
 // runs a scalar "finisher" on thread 0.

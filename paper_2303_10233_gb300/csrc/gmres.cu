@@ -495,8 +495,9 @@ static eth_status q1_vcycle(eth_grid* g, Work* w, const T* r, T* z, const int* d
   k_q1_j0<T><<<gb(m), 256, 0, g->s>>>(m, (T)Q.omega, L0.dinv, r, L0.b, L0.x, done);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
-  ETH_TRY(vcycle_q1_from<T>(g, Q, 1, 1, done));
-  k_copy_t<T><<<gb(m), 256, 0, g->s>>>(m, L0.x, z);
+  const T* res = nullptr;
+  ETH_TRY(vcycle_q1_from<T>(g, Q, 1, 1, done, &res));
+  k_copy_t<T><<<gb(m), 256, 0, g->s>>>(m, res, z);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
   return ETH_OK;
@@ -562,7 +563,7 @@ static eth_status q1_mass_inv(eth_grid* g, GMRESWork* G, const double* b, T* x, 
 // velocity part of a block-triangular preconditioner: z_u = V_F(r_u - B^T z_p)
 template <class T>
 static eth_status vel_part(eth_grid* g, Work* w, const eth_opts* o, const double* ru, const double* zp, bool p0, double* zu,
-                           const int* done) {
+                           const int* done, bool adj) {
   GMRESWork* G = w->gm;
   Q2Params<double, double, T> P{};
   P.n = g->n; P.hx = (T)g->hx; P.hy = (T)g->hy; P.nu = 0;
@@ -570,12 +571,12 @@ static eth_status vel_part(eth_grid* g, Work* w, const eth_opts* o, const double
   if (p0) ETH_CUDA((launch_q2<double, double, T, QF_PIN | QF_P0 | QF_UOUT, EPI_BSUB>(P, g->s)));
   else ETH_CUDA((launch_q2<double, double, T, QF_PIN | QF_UOUT, EPI_BSUB>(P, g->s)));
   g->launches++;
-  return vcycle_vel<T>(g, vel_hier<T>(w), G->t, zu, o->mg_pre, o->mg_post, done, nullptr, 0);
+  return vcycle_vel<T>(g, adj ? vel_hier_t<T>(w) : vel_hier<T>(w), G->t, zu, o->mg_pre, o->mg_post, done, nullptr, 0);
 }
 
 // Step I preconditioner on [r_u; r_p1]: z_p = -Ap^+ F1 Q1^{-1} r_p, z_u = V_F(r_u - B1^T z_p)
 template <class T>
-static eth_status precond_pcd(eth_grid* g, Work* w, const eth_opts* o, const double* r, double* z, const int* done) {
+static eth_status precond_pcd(eth_grid* g, Work* w, const eth_opts* o, const double* r, double* z, const int* done, bool adj) {
   GMRESWork* G = w->gm;
   const size_t nu2 = 2 * (size_t)g->nv;
   const int m = g->n1;
@@ -601,12 +602,12 @@ static eth_status precond_pcd(eth_grid* g, Work* w, const eth_opts* o, const dou
   k_pcd_out<T><<<gb(m), 256, 0, g->s>>>(m, sol, z + nu2, G->gs, -1.0);
   ETH_CUDA(cudaGetLastError());
   g->launches += 2;
-  return vel_part<T>(g, w, o, r, z + nu2, false, z, done);
+  return vel_part<T>(g, w, o, r, z + nu2, false, z, done, adj);
 }
 
 // Step II preconditioner M_1: z_p = -nu M_Q^+ r_p (k projected out), z_u = V_F(r_u - B^T z_p)
 template <class T>
-static eth_status precond_m1(eth_grid* g, Work* w, const eth_opts* o, const double* r, double* z, const int* done) {
+static eth_status precond_m1(eth_grid* g, Work* w, const eth_opts* o, const double* r, double* z, const int* done, bool adj) {
   const size_t nu2 = 2 * (size_t)g->nv;
   const int nb = vblocks((size_t)g->n1 + g->n0);
   k_psums<0><<<nb, 256, 0, g->s>>>(nu2, (size_t)g->n1, (size_t)g->n0, r, slot_of(g, SL_VSUM, nb, FIN_VSUMS));
@@ -614,12 +615,12 @@ static eth_status precond_m1(eth_grid* g, Work* w, const eth_opts* o, const doub
   g->launches++;
   Slot gs = slot_of(g, SL_GEN, mq_blocks(g), FIN_STORE);
   ETH_TRY(precond_pressure<T>(g, q1_hier<T>(w), r + nu2, z + nu2, gs, 0, done, g->s));
-  return vel_part<T>(g, w, o, r, z + nu2, true, z, done);
+  return vel_part<T>(g, w, o, r, z + nu2, true, z, done, adj);
 }
 
 // y = K x for the active system (stage 1: reduced [F B1^T; B1 0], stage 2: full)
 static eth_status sys_apply(eth_grid* g, int stage, bool fp32, bool trans, const double* x, double* y) {
-  const eth_op op = stage == 1 ? ETH_OP_K1 : (trans ? ETH_OP_KT : ETH_OP_K);
+  const eth_op op = stage == 1 ? (trans ? ETH_OP_K1T : ETH_OP_K1) : (trans ? ETH_OP_KT : ETH_OP_K);
   return op_apply(g, op, fp32, x, y);
 }
 
@@ -653,8 +654,8 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
     for (int j = 0; j < m && its < maxit; ++j) {
       double* Vj = G->V + (size_t)j * ld;
       double* Zj = G->Z + (size_t)j * ld;
-      if (stage == 1) ETH_TRY(precond_pcd<T>(g, w, o, Vj, Zj, done));
-      else ETH_TRY(precond_m1<T>(g, w, o, Vj, Zj, done));
+      if (stage == 1) ETH_TRY(precond_pcd<T>(g, w, o, Vj, Zj, done, adj));
+      else ETH_TRY(precond_m1<T>(g, w, o, Vj, Zj, done, adj));
       ETH_TRY(sys_apply(g, stage, fp32, adj, Zj, G->w));
       double* h1 = &G->gs->h1[0];
       double* h2 = &G->gs->h2[0];
@@ -743,11 +744,11 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
   return st->relres_true <= eta * (1.0 + 1e-9) ? ETH_OK : ETH_ENOTCONV;
 }
 
-eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint) {
+eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* bsrc) {
   const int m = std::max(1, std::min(o->restart, GM_MAX));
   ETH_TRY(gm_alloc(g, w, m));
   // consistent right-hand side (e1 / e0 components removed)
-  ETH_CUDA(cudaMemcpyAsync(w->bp, g->b, (size_t)g->nt * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaMemcpyAsync(w->bp, bsrc, (size_t)g->nt * 8, cudaMemcpyDeviceToDevice, g->s));
   ETH_TRY(canonicalize(g, w->bp));
   if (o->precision == ETH_MIXED) {
     ETH_TRY(ensure_hier<float>(g, w, o));

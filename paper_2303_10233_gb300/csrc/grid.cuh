@@ -14,6 +14,7 @@ struct Level {
   double hx = 0, hy = 0;
   double nu = 1.0;       // viscosity of the level operator
   double sd = 0.0;       // streamline-diffusion coefficient of the level (coarse Oseen levels)
+  bool trans = false;    // transposed convection (adjoint operator F^T)
   T* w = nullptr;        // Q2 wind (2 N_v), velocity levels with convection
   T* dinv = nullptr;     // inverse diagonal (N_v for velocity, (n+1)^2 for Q1)
   T* x = nullptr;        // iterate
@@ -30,7 +31,9 @@ struct Hier {
   int* coarse_idx = nullptr; // lattice index of each coarse unknown
   int ncoarse = 0;
   bool q1 = false;           // pressure (Q1 Laplacian) hierarchy
+  bool trans = false;        // velocity hierarchy of F^T (adjoint)
   bool built = false;
+  bool fused = true;         // fused level kernels + single-CTA coarse V-cycle
   double omega = 0.8;
 };
 

@@ -80,7 +80,7 @@ __global__ void k_q2_jacobi0(int n, T omega, const T* __restrict__ dinv, const T
     const size_t g = k < nv ? k : k - nv;
     const int j = (int)(g / N), i = (int)(g - (size_t)j * N);
     const bool bnd = i == 0 || j == 0 || i == N - 1 || j == N - 1;
-    const T b = bnd ? T(0) : (T)bin[k];
+    const T b = bnd ? T(0) : cvt<T, TI>(bin[k]);
     if (bc != (const T*)bin) bc[k] = b;
     x[k] = omega * dinv[g] * b;
   }
@@ -372,8 +372,9 @@ static std::vector<int> level_sizes(int n, int nmin) {
 }
 
 template <class T>
-eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art) {
+eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art, bool trans) {
   mg_free(H);
+  H.trans = trans;
   const std::vector<int> ns = level_sizes(g->n, nmin);
   if (ns.back() > 32) { set_error("multigrid: n=%d does not coarsen to <= 32 (n must be c*2^k, c <= 32)", g->n); return ETH_EINVAL; }
   const bool conv = g->kind == ETH_OSEEN;
@@ -393,6 +394,7 @@ eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art) {
     L.hy = g->hy * (g->n / L.n);
     L.nu = g->nu;
     L.sd = (l > 0 && conv) ? art : 0.0;
+    L.trans = trans && conv;
     const size_t N = 2 * (size_t)L.n + 1, nv = N * N;
     ETH_CUDA(cudaMalloc((void**)&L.dinv, nv * sizeof(T)));
     ETH_CUDA(cudaMalloc((void**)&L.x, 2 * nv * sizeof(T)));
@@ -432,6 +434,9 @@ eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art) {
   ETH_CUDA(cudaStreamSynchronize(g->s));
   cudaFree(D);
   cudaFree(wd);
+  if (trans)
+    for (int i = 0; i < m; ++i)
+      for (int j = i + 1; j < m; ++j) std::swap(h[(size_t)i * m + j], h[(size_t)j * m + i]);
   if (!invert(h, m)) { set_error("multigrid: singular coarse operator"); return ETH_EINVAL; }
   ETH_TRY(upload<T>(h, &H.coarse_inv, g->s));
   H.ncoarse = m;
@@ -487,6 +492,321 @@ eth_status mg_build_q1(eth_grid* g, Hier<T>& H, int nmin) {
 }
 
 // ---------------------------------------------------------------------------
+// Single-CTA V-cycle over the coarsest levels, entirely in shared memory.
+// One launch replaces the (smoothing, residual, transfer) launches of every
+// level with n <= the coarse threshold; each operator application is an
+// element loop in four colour phases (elements of one colour share no node).
+// ---------------------------------------------------------------------------
+constexpr int CMAXL = 6;
+template <class T>
+struct CoarseQ2 {
+  int nlev;
+  int n[CMAXL];
+  T hx[CMAXL], hy[CMAXL], nu[CMAXL], sd[CMAXL];
+  const T* dinv[CMAXL];
+  const T* w[CMAXL];
+};
+
+template <class T, int FL>
+__device__ void cq2_residual(int n, T hx, T hy, T nu, T sd, const T* __restrict__ w, const T* X, const T* B, T* R) {
+  const int N = 2 * n + 1, nv = N * N;
+  for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) R[k] = B[k];
+  __syncthreads();
+  const T ihx = T(1) / hx, ihy = T(1) / hy, area = hx * hy;
+  for (int col = 0; col < 4; ++col) {
+    const int cx = col & 1, cy = col >> 1;
+    const int nx = (n - cx + 1) / 2, ny = (n - cy + 1) / 2;
+    for (int e = threadIdx.x; e < nx * ny; e += blockDim.x) {
+      const int ex = 2 * (e % nx) + cx, ey = 2 * (e / nx) + cy;
+      T U[2][9], Wn[2][9], P1[4] = {0, 0, 0, 0}, Y[2][9], YP1[4], YP0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int g = (2 * ey + b) * N + 2 * ex + a;
+          U[0][b * 3 + a] = X[g];
+          U[1][b * 3 + a] = X[g + nv];
+          if (FL & QF_CONV) { Wn[0][b * 3 + a] = w[g]; Wn[1][b * 3 + a] = w[g + nv]; }
+        }
+      q2_elem<T, FL>(U, Wn, P1, T(0), nu, ihx, ihy, area, sd, Y, YP1, YP0);
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          const int g = (2 * ey + b) * N + 2 * ex + a;
+          R[g] -= Y[0][b * 3 + a];
+          R[g + nv] -= Y[1][b * 3 + a];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+template <class T, int FL>
+__global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __restrict__ Ainv, int m,
+                                                        const T* __restrict__ bin, T* __restrict__ xout, T omega,
+                                                        int pre, int post, const int* done) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  T *X[CMAXL], *B[CMAXL], *R[CMAXL];
+  size_t off = 0;
+  for (int l = 0; l < L.nlev; ++l) {
+    const int N = 2 * L.n[l] + 1;
+    X[l] = sm + off; off += 2 * N * N;
+    B[l] = sm + off; off += 2 * N * N;
+    R[l] = sm + off; off += 2 * N * N;
+  }
+  {
+    const int N = 2 * L.n[0] + 1;
+    for (int k = threadIdx.x; k < 2 * N * N; k += blockDim.x) B[0][k] = bin[k];
+  }
+  __syncthreads();
+  for (int l = 0; l < L.nlev - 1; ++l) {
+    const int n = L.n[l], N = 2 * n + 1, nv = N * N;
+    for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) {
+      const int g = k < nv ? k : k - nv;
+      X[l][k] = omega * L.dinv[l][g] * B[l][k];   // dinv and B vanish on the boundary
+    }
+    __syncthreads();
+    for (int s = 1; s < pre; ++s) {
+      cq2_residual<T, FL>(n, L.hx[l], L.hy[l], L.nu[l], L.sd[l], L.w[l], X[l], B[l], R[l]);
+      for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] += omega * L.dinv[l][k < nv ? k : k - nv] * R[l][k];
+      __syncthreads();
+    }
+    cq2_residual<T, FL>(n, L.hx[l], L.hy[l], L.nu[l], L.sd[l], L.w[l], X[l], B[l], R[l]);
+    const int nc = L.n[l + 1], Nc = 2 * nc + 1, nvc = Nc * Nc;
+    for (int node = threadIdx.x; node < nvc; node += blockDim.x) {
+      const int J = node / Nc, I = node - J * Nc;
+      T s0 = 0, s1 = 0;
+      if (!(I == 0 || J == 0 || I == Nc - 1 || J == Nc - 1)) {
+        int ox[5], oy[5];
+        float wx[5], wy[5];
+        const int nx = q2_rweights(I, ox, wx), ny = q2_rweights(J, oy, wy);
+        for (int u = 0; u < ny; ++u)
+          for (int v = 0; v < nx; ++v) {
+            const int f = (2 * J + oy[u]) * N + 2 * I + ox[v];
+            const T c = (T)(wx[v] * wy[u]);
+            s0 += c * R[l][f];
+            s1 += c * R[l][f + nv];
+          }
+      }
+      B[l + 1][node] = s0;
+      B[l + 1][node + nvc] = s1;
+    }
+    __syncthreads();
+  }
+  {
+    const int l = L.nlev - 1, n = L.n[l], N = 2 * n + 1, M = N - 2, nv = N * N;
+    for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * m; t += blockDim.x) {
+      const int c = t / m, r = t - c * m;
+      T acc = 0;
+      for (int k = 0; k < m; ++k) acc += Ainv[(size_t)r * m + k] * B[l][c * nv + (k / M + 1) * N + (k % M + 1)];
+      X[l][c * nv + (r / M + 1) * N + (r % M + 1)] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = L.nlev - 2; l >= 0; --l) {
+    const int n = L.n[l], N = 2 * n + 1, nv = N * N;
+    const int nc = L.n[l + 1], Nc = 2 * nc + 1, nvc = Nc * Nc;
+    for (int node = threadIdx.x; node < nv; node += blockDim.x) {
+      const int j = node / N, i = node - j * N;
+      if (i == 0 || j == 0 || i == N - 1 || j == N - 1) continue;
+      int cx[3], cy[3];
+      float wx[3], wy[3];
+      const int nx = q2_pweights(i, cx, wx), ny = q2_pweights(j, cy, wy);
+      T s0 = 0, s1 = 0;
+      for (int u = 0; u < ny; ++u)
+        for (int v = 0; v < nx; ++v) {
+          const int c = cy[u] * Nc + cx[v];
+          const T f = (T)(wx[v] * wy[u]);
+          s0 += f * X[l + 1][c];
+          s1 += f * X[l + 1][c + nvc];
+        }
+      X[l][node] += s0;
+      X[l][node + nv] += s1;
+    }
+    __syncthreads();
+    for (int s = 0; s < post; ++s) {
+      cq2_residual<T, FL>(n, L.hx[l], L.hy[l], L.nu[l], L.sd[l], L.w[l], X[l], B[l], R[l]);
+      for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] += omega * L.dinv[l][k < nv ? k : k - nv] * R[l][k];
+      __syncthreads();
+    }
+  }
+  {
+    const int N = 2 * L.n[0] + 1;
+    for (int k = threadIdx.x; k < 2 * N * N; k += blockDim.x) xout[k] = X[0][k];
+  }
+}
+
+// Q1 Laplacian counterpart (natural boundary; pseudo-inverse on the coarsest grid)
+template <class T>
+struct CoarseQ1 {
+  int nlev;
+  int n[CMAXL];
+  T hx[CMAXL], hy[CMAXL];
+  const T* dinv[CMAXL];
+};
+
+template <class T>
+__device__ void cq1_residual(int n, T hx, T hy, const T* X, const T* B, T* R) {
+  const int M = n + 1;
+  const T rxy = hy / hx, ryx = hx / hy;
+  for (int node = threadIdx.x; node < M * M; node += blockDim.x) {
+    const int J = node / M, I = node - J * M;
+    T acc = 0;
+    for (int ey = J - 1; ey <= J; ++ey) {
+      if (ey < 0 || ey >= n) continue;
+      const int d = J - ey;
+      for (int ex = I - 1; ex <= I; ++ex) {
+        if (ex < 0 || ex >= n) continue;
+        const int c = I - ex;
+        for (int dd = 0; dd < 2; ++dd)
+          for (int cc = 0; cc < 2; ++cc) {
+            const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
+            acc += kc * X[(ey + dd) * M + ex + cc];
+          }
+      }
+    }
+    R[node] = B[node] - acc;
+  }
+  __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(1024) k_q1_coarse_vc(CoarseQ1<T> L, const T* __restrict__ Apinv, int m,
+                                                        const T* __restrict__ bin, T* __restrict__ xout, T omega,
+                                                        const int* done) {
+  if (done != nullptr && *done) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* sm = reinterpret_cast<T*>(smraw);
+  T *X[CMAXL], *B[CMAXL], *R[CMAXL];
+  size_t off = 0;
+  for (int l = 0; l < L.nlev; ++l) {
+    const int M = L.n[l] + 1;
+    X[l] = sm + off; off += M * M;
+    B[l] = sm + off; off += M * M;
+    R[l] = sm + off; off += M * M;
+  }
+  {
+    const int M = L.n[0] + 1;
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) B[0][k] = bin[k];
+  }
+  __syncthreads();
+  for (int l = 0; l < L.nlev - 1; ++l) {
+    const int n = L.n[l], M = n + 1;
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) X[l][k] = omega * L.dinv[l][k] * B[l][k];
+    __syncthreads();
+    cq1_residual<T>(n, L.hx[l], L.hy[l], X[l], B[l], R[l]);
+    const int Mc = L.n[l + 1] + 1;
+    for (int node = threadIdx.x; node < Mc * Mc; node += blockDim.x) {
+      const int J = node / Mc, I = node - J * Mc;
+      T s = 0;
+      for (int dy = -1; dy <= 1; ++dy) {
+        const int j = 2 * J + dy;
+        if (j < 0 || j >= M) continue;
+        for (int dx = -1; dx <= 1; ++dx) {
+          const int i = 2 * I + dx;
+          if (i < 0 || i >= M) continue;
+          s += (dy == 0 ? T(1) : T(0.5)) * (dx == 0 ? T(1) : T(0.5)) * R[l][j * M + i];
+        }
+      }
+      B[l + 1][node] = s;
+    }
+    __syncthreads();
+  }
+  {
+    const int l = L.nlev - 1;
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+      T acc = 0;
+      for (int k = 0; k < m; ++k) acc += Apinv[(size_t)r * m + k] * B[l][k];
+      X[l][r] = acc;
+    }
+    __syncthreads();
+  }
+  for (int l = L.nlev - 2; l >= 0; --l) {
+    const int n = L.n[l], M = n + 1, Mc = L.n[l + 1] + 1;
+    for (int node = threadIdx.x; node < M * M; node += blockDim.x) {
+      const int j = node / M, i = node - j * M;
+      const int I0 = i >> 1, I1 = (i + 1) >> 1, J0 = j >> 1, J1 = (j + 1) >> 1;
+      X[l][node] += T(0.25) * (X[l + 1][J0 * Mc + I0] + X[l + 1][J0 * Mc + I1] + X[l + 1][J1 * Mc + I0] + X[l + 1][J1 * Mc + I1]);
+    }
+    __syncthreads();
+    cq1_residual<T>(n, L.hx[l], L.hy[l], X[l], B[l], R[l]);
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) X[l][k] += omega * L.dinv[l][k] * R[l][k];
+    __syncthreads();
+  }
+  {
+    const int M = L.n[0] + 1;
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) xout[k] = X[0][k];
+  }
+}
+
+// Q1 first sweep from zero fused with the residual: x = omega D^{-1} b, r = b - K1 x
+template <class T>
+__global__ void k_q1_jr(int n, T hx, T hy, T omega, const T* __restrict__ dinv, const T* __restrict__ b,
+                        T* __restrict__ x, T* __restrict__ r, const int* done) {
+  if (done != nullptr && *done) return;
+  const int M = n + 1;
+  const T rxy = hy / hx, ryx = hx / hy;
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < M * M; node += gridDim.x * blockDim.x) {
+    const int J = node / M, I = node - J * M;
+    T acc = 0;
+    for (int ey = J - 1; ey <= J; ++ey) {
+      if (ey < 0 || ey >= n) continue;
+      const int d = J - ey;
+      for (int ex = I - 1; ex <= I; ++ex) {
+        if (ex < 0 || ex >= n) continue;
+        const int c = I - ex;
+        for (int dd = 0; dd < 2; ++dd)
+          for (int cc = 0; cc < 2; ++cc) {
+            const int q = (ey + dd) * M + ex + cc;
+            const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
+            acc += kc * omega * dinv[q] * b[q];
+          }
+      }
+    }
+    const T xv = omega * dinv[node] * b[node];
+    x[node] = xv;
+    r[node] = b[node] - acc;
+  }
+}
+
+// Q1 prolongation fused with the smoothing sweep: x' = x + P xc ; y = x' + omega D^{-1} (b - K1 x')
+template <class T>
+__global__ void k_q1_ps(int n, T hx, T hy, T omega, const T* __restrict__ dinv, const T* __restrict__ b,
+                        const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ y, const int* done) {
+  if (done != nullptr && *done) return;
+  const int M = n + 1, Mc = n / 2 + 1;
+  const T rxy = hy / hx, ryx = hx / hy;
+  auto xcorr = [&](int jj, int ii) -> T {
+    const int I0 = ii >> 1, I1 = (ii + 1) >> 1, J0 = jj >> 1, J1 = (jj + 1) >> 1;
+    return x[jj * M + ii] + T(0.25) * (xc[J0 * Mc + I0] + xc[J0 * Mc + I1] + xc[J1 * Mc + I0] + xc[J1 * Mc + I1]);
+  };
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < M * M; node += gridDim.x * blockDim.x) {
+    const int J = node / M, I = node - J * M;
+    T acc = 0;
+    for (int ey = J - 1; ey <= J; ++ey) {
+      if (ey < 0 || ey >= n) continue;
+      const int d = J - ey;
+      for (int ex = I - 1; ex <= I; ++ex) {
+        if (ex < 0 || ex >= n) continue;
+        const int c = I - ex;
+        for (int dd = 0; dd < 2; ++dd)
+          for (int cc = 0; cc < 2; ++cc) {
+            const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
+            acc += kc * xcorr(ey + dd, ex + cc);
+          }
+      }
+    }
+    const T xv = xcorr(J, I);
+    y[node] = xv + omega * dinv[node] * (b[node] - acc);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // V-cycles
 // ---------------------------------------------------------------------------
 template <class T, class TO, int EPI, int CF>
@@ -509,6 +829,8 @@ static eth_status q2_level(eth_grid* g, const Level<T>& L, const T* x, TO* y, T 
 template <class T, class TO, int EPI>
 static eth_status q2_level_d(eth_grid* g, const Level<T>& L, const T* x, TO* y, T omega, const TO* bsrc,
                              const int* done, const Slot* slot = nullptr, int slot_off = 0, const TO* dv = nullptr) {
+  if (L.w != nullptr && L.trans && L.sd > 0.0) return q2_level<T, TO, EPI, QF_CONV | QF_TRANS | QF_SD>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
+  if (L.w != nullptr && L.trans) return q2_level<T, TO, EPI, QF_CONV | QF_TRANS>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
   if (L.w != nullptr && L.sd > 0.0) return q2_level<T, TO, EPI, QF_CONV | QF_SD>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
   if (L.w != nullptr) return q2_level<T, TO, EPI, QF_CONV>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
   return q2_level<T, TO, EPI, 0>(g, L, x, y, omega, bsrc, done, slot, slot_off, dv);
@@ -516,12 +838,21 @@ static eth_status q2_level_d(eth_grid* g, const Level<T>& L, const T* x, TO* y, 
 
 int vel_final_blocks(int n) { return q2_blocks(n); }
 
+template <class T> static int vel_fused_start(const Hier<T>& H);
+template <class T>
+static eth_status vcycle_vel_fused(eth_grid* g, Hier<T>& H, const double* v, double* z, int pre, int post,
+                                   const int* done, const Slot* slot, int slot_off, int Lc);
+
 template <class T>
 eth_status vcycle_vel(eth_grid* g, Hier<T>& H, const double* v, double* z, int pre, int post, const int* done,
                       const Slot* slot, int slot_off) {
   const int nl = (int)H.lv.size();
   const T om = (T)H.omega;
   if (nl < 2) { set_error("vcycle: hierarchy needs two levels"); return ETH_EINVAL; }
+  if (H.fused) {
+    const int Lc = vel_fused_start(H);
+    if (Lc >= 1) return vcycle_vel_fused<T>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
+  }
   // descend
   for (int l = 0; l < nl - 1; ++l) {
     Level<T>& L = H.lv[l];
@@ -594,10 +925,40 @@ static eth_status q1_level(eth_grid* g, const Level<T>& L, const T* x, T* y, int
   return ETH_OK;
 }
 
+template <class T> static int q1_fused_start(const Hier<T>& H);
 template <class T>
-eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done) {
+static eth_status q1_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, const int* done);
+
+template <class T>
+eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done, const T** result) {
   const int nl = (int)H.lv.size();
   const T om = (T)H.omega;
+  *result = H.lv[0].x;
+  if (H.fused && pre == 1 && post == 1) {
+    const int Lc = q1_fused_start(H);
+    if (Lc >= 1) {
+      std::vector<const T*> res(nl, nullptr);
+      for (int l = 0; l < Lc; ++l) {
+        Level<T>& L = H.lv[l];
+        k_q1_jr<T><<<q1_blocks(L.n), 256, 0, g->s>>>(L.n, (T)L.hx, (T)L.hy, om, L.dinv, L.b, L.x, L.r, done);
+        const Level<T>& Cn = H.lv[l + 1];
+        k_q1_restrict<T><<<gsize((size_t)(Cn.n + 1) * (Cn.n + 1)), 256, 0, g->s>>>(Cn.n, L.r, Cn.b, done);
+        ETH_CUDA(cudaGetLastError());
+        g->launches += 2;
+      }
+      ETH_TRY(q1_coarse_launch<T>(g, H, Lc, done));
+      res[Lc] = H.lv[Lc].x;
+      for (int l = Lc - 1; l >= 0; --l) {
+        Level<T>& L = H.lv[l];
+        k_q1_ps<T><<<q1_blocks(L.n), 256, 0, g->s>>>(L.n, (T)L.hx, (T)L.hy, om, L.dinv, L.b, L.x, res[l + 1], L.t, done);
+        ETH_CUDA(cudaGetLastError());
+        g->launches++;
+        res[l] = L.t;
+      }
+      *result = res[0];
+      return ETH_OK;
+    }
+  }
   for (int l = 0; l < nl - 1; ++l) {
     Level<T>& L = H.lv[l];
     const size_t tot = (size_t)(L.n + 1) * (L.n + 1);
@@ -638,13 +999,177 @@ eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int*
   return ETH_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// fused V-cycles: (Jacobi-from-zero + residual) and (prolongation + smoothing)
+// in one tile launch per level, single-CTA shared-memory V-cycle below the
+// coarse threshold.
+// ---------------------------------------------------------------------------
+template <class T> static int q2_coarse_threshold() { return sizeof(T) == 4 ? 32 : 16; }
+template <class T> static int q1_coarse_threshold() { return 64; }
+
+template <class T, class TI, int CF>
+static eth_status q2_jr(eth_grid* g, Level<T>& L, const TI* b, T* bcopy, T omega, const int* done) {
+  Q2Params<TI, T, T> P{};
+  P.n = L.n; P.hx = (T)L.hx; P.hy = (T)L.hy; P.nu = (T)L.nu; P.sd = (T)L.sd;
+  P.w = L.w; P.dinv = L.dinv; P.omega = omega; P.done = done;
+  P.bx = b; P.y = L.r; P.y2 = L.x; P.bcopy = bcopy;
+  ETH_CUDA((launch_q2<TI, T, T, QF_DIFF | QF_XIN | QF_UOUT | QF_SRC_JB | CF, EPI_JR>(P, g->s)));
+  g->launches++;
+  return ETH_OK;
+}
+
+template <class T, class TO, int CF>
+static eth_status q2_ps(eth_grid* g, Level<T>& L, const T* x, const T* xc, TO* y, T omega, const TO* bsrc,
+                        const int* done, const Slot* slot, int slot_off, const TO* dv) {
+  Q2Params<T, TO, T> P{};
+  P.n = L.n; P.hx = (T)L.hx; P.hy = (T)L.hy; P.nu = (T)L.nu; P.sd = (T)L.sd;
+  P.w = L.w; P.dinv = L.dinv; P.omega = omega; P.done = done;
+  P.x = x; P.xc = xc; P.b = L.b; P.y = y; P.bsrc = bsrc;
+  constexpr int F0 = QF_DIFF | QF_XIN | QF_UOUT | QF_SRC_XPC | CF;
+  if (slot) {
+    P.slot = *slot; P.slot_off = slot_off; P.dv = dv;
+    ETH_CUDA((launch_q2<T, TO, T, F0 | QF_DOT, EPI_SMOOTH>(P, g->s)));
+  } else {
+    ETH_CUDA((launch_q2<T, TO, T, F0, EPI_SMOOTH>(P, g->s)));
+  }
+  g->launches++;
+  return ETH_OK;
+}
+
+template <class T, int FL>
+static eth_status q2_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, int pre, int post, const int* done) {
+  CoarseQ2<T> C{};
+  C.nlev = (int)H.lv.size() - Lc;
+  if (C.nlev > CMAXL) { set_error("multigrid: too many coarse levels"); return ETH_EINVAL; }
+  size_t smem = 0;
+  for (int l = 0; l < C.nlev; ++l) {
+    const Level<T>& L = H.lv[Lc + l];
+    C.n[l] = L.n; C.hx[l] = (T)L.hx; C.hy[l] = (T)L.hy; C.nu[l] = (T)L.nu; C.sd[l] = (T)L.sd;
+    C.dinv[l] = L.dinv; C.w[l] = L.w;
+    const size_t N = 2 * (size_t)L.n + 1;
+    smem += 3 * 2 * N * N * sizeof(T);
+  }
+  static bool set = false;
+  if (!set) {
+    ETH_CUDA(cudaFuncSetAttribute(k_q2_coarse_vc<T, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    set = true;
+  }
+  if (smem > 227 * 1024) { set_error("multigrid: coarse levels exceed shared memory"); return ETH_EINVAL; }
+  k_q2_coarse_vc<T, FL><<<1, 512, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, pre, post, done);
+  ETH_CUDA(cudaGetLastError());
+  g->launches++;
+  return ETH_OK;
+}
+
+template <class T, int CF>
+static eth_status vcycle_vel_fused_cf(eth_grid* g, Hier<T>& H, const double* v, double* z, int pre, int post,
+                                      const int* done, const Slot* slot, int slot_off, int Lc) {
+  const T om = (T)H.omega;
+  std::vector<T*> res(H.lv.size(), nullptr);
+  for (int l = 0; l < Lc; ++l) {
+    Level<T>& L = H.lv[l];
+    const size_t N = 2 * (size_t)L.n + 1, nv = N * N;
+    if (l == 0) ETH_TRY((q2_jr<T, double, CF>(g, L, v, L.b, om, done)));
+    else ETH_TRY((q2_jr<T, T, CF>(g, L, L.b, nullptr, om, done)));
+    for (int s = 1; s < pre; ++s) {
+      ETH_TRY((q2_level<T, T, EPI_SMOOTH, CF>(g, L, L.x, L.t, om, nullptr, done, nullptr, 0, nullptr)));
+      ETH_CUDA(cudaMemcpyAsync(L.x, L.t, 2 * nv * sizeof(T), cudaMemcpyDeviceToDevice, g->s));
+      ETH_TRY((q2_level<T, T, EPI_RESID, CF>(g, L, L.x, L.r, om, nullptr, done, nullptr, 0, nullptr)));
+    }
+    const Level<T>& Cn = H.lv[l + 1];
+    const size_t Nc = 2 * (size_t)Cn.n + 1;
+    k_q2_restrict<T><<<gsize(Nc * Nc), 256, 0, g->s>>>(Cn.n, L.r, Cn.b, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+  }
+  constexpr int FL = QF_DIFF | QF_XIN | QF_UOUT | CF;
+  ETH_TRY((q2_coarse_launch<T, FL>(g, H, Lc, pre, post, done)));
+  res[Lc] = H.lv[Lc].x;
+  for (int l = Lc - 1; l >= 0; --l) {
+    Level<T>& L = H.lv[l];
+    const bool last0 = (l == 0 && post == 1);
+    if (last0) {
+      ETH_TRY((q2_ps<T, double, CF>(g, L, L.x, res[l + 1], z, om, v, done, slot, slot_off, v)));
+      continue;
+    }
+    ETH_TRY((q2_ps<T, T, CF>(g, L, L.x, res[l + 1], L.t, om, nullptr, done, nullptr, 0, nullptr)));
+    T* cur = L.t;
+    T* oth = L.x;
+    for (int s = 1; s < post; ++s) {
+      if (l == 0 && s == post - 1) {
+        ETH_TRY((q2_level<T, double, EPI_SMOOTH, CF>(g, L, cur, z, om, v, done, slot, slot_off, v)));
+        cur = nullptr;
+        break;
+      }
+      ETH_TRY((q2_level<T, T, EPI_SMOOTH, CF>(g, L, cur, oth, om, nullptr, done, nullptr, 0, nullptr)));
+      std::swap(cur, oth);
+    }
+    res[l] = cur;
+  }
+  return ETH_OK;
+}
+
+template <class T>
+static eth_status vcycle_vel_fused(eth_grid* g, Hier<T>& H, const double* v, double* z, int pre, int post,
+                                   const int* done, const Slot* slot, int slot_off, int Lc) {
+  const Level<T>& L0 = H.lv[0];
+  // coarse levels carry streamline diffusion (sd > 0), the finest does not (sd = 0 gives delta = 0),
+  // so one instantiation with QF_SD serves all levels.
+  const bool sd = L0.w != nullptr && H.lv.size() > 1 && H.lv[1].sd > 0.0;
+  if (L0.w != nullptr && H.trans && sd) return vcycle_vel_fused_cf<T, QF_CONV | QF_TRANS | QF_SD>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
+  if (L0.w != nullptr && H.trans) return vcycle_vel_fused_cf<T, QF_CONV | QF_TRANS>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
+  if (sd) return vcycle_vel_fused_cf<T, QF_CONV | QF_SD>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
+  if (L0.w != nullptr) return vcycle_vel_fused_cf<T, QF_CONV>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
+  return vcycle_vel_fused_cf<T, 0>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
+}
+
+template <class T>
+static eth_status q1_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, const int* done) {
+  CoarseQ1<T> C{};
+  C.nlev = (int)H.lv.size() - Lc;
+  if (C.nlev > CMAXL) { set_error("multigrid: too many Q1 coarse levels"); return ETH_EINVAL; }
+  size_t smem = 0;
+  for (int l = 0; l < C.nlev; ++l) {
+    const Level<T>& L = H.lv[Lc + l];
+    C.n[l] = L.n; C.hx[l] = (T)L.hx; C.hy[l] = (T)L.hy; C.dinv[l] = L.dinv;
+    const size_t M = (size_t)L.n + 1;
+    smem += 3 * M * M * sizeof(T);
+  }
+  static bool set = false;
+  if (!set) {
+    ETH_CUDA(cudaFuncSetAttribute(k_q1_coarse_vc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+    set = true;
+  }
+  if (smem > 227 * 1024) { set_error("multigrid: Q1 coarse levels exceed shared memory"); return ETH_EINVAL; }
+  k_q1_coarse_vc<T><<<1, 1024, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, done);
+  ETH_CUDA(cudaGetLastError());
+  g->launches++;
+  return ETH_OK;
+}
+
+template <class T>
+static int vel_fused_start(const Hier<T>& H) {
+  const int thr = q2_coarse_threshold<T>();
+  for (int l = 0; l < (int)H.lv.size(); ++l)
+    if (H.lv[l].n <= thr) return ((int)H.lv.size() - l > CMAXL) ? -1 : l;
+  return -1;
+}
+template <class T>
+static int q1_fused_start(const Hier<T>& H) {
+  const int thr = q1_coarse_threshold<T>();
+  for (int l = 0; l < (int)H.lv.size(); ++l)
+    if (H.lv[l].n <= thr) return ((int)H.lv.size() - l > CMAXL) ? -1 : l;
+  return -1;
+}
+
 #define ETH_MG_INST(T)                                                                                    \
-  template eth_status mg_build_vel<T>(eth_grid*, Hier<T>&, int, double);                                 \
+  template eth_status mg_build_vel<T>(eth_grid*, Hier<T>&, int, double, bool);                                 \
   template eth_status mg_build_q1<T>(eth_grid*, Hier<T>&, int);                                          \
   template void mg_free<T>(Hier<T>&);                                                                    \
   template eth_status vcycle_vel<T>(eth_grid*, Hier<T>&, const double*, double*, int, int, const int*,   \
                                     const Slot*, int);                                                   \
-  template eth_status vcycle_q1_from<T>(eth_grid*, Hier<T>&, int, int, const int*);
+  template eth_status vcycle_q1_from<T>(eth_grid*, Hier<T>&, int, int, const int*, const T**);
 ETH_MG_INST(float)
 ETH_MG_INST(double)
 

@@ -18,7 +18,7 @@
 namespace eth {
 
 template <class T>
-eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art);
+eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art, bool trans = false);
 template <class T>
 eth_status mg_build_q1(eth_grid* g, Hier<T>& H, int nmin);
 template <class T>
@@ -30,10 +30,10 @@ void mg_free(Hier<T>& H);
 template <class T>
 eth_status vcycle_vel(eth_grid* g, Hier<T>& H, const double* v, double* z, int pre, int post, const int* done,
                       const Slot* slot, int slot_off);
-// Q1 V-cycle on level 0 whose b and x (after the first sweep) are already set;
-// result left in H.lv[0].x (type T).
+// Q1 V-cycle on level 0 whose b (and, for the unfused path, x after the first
+// sweep) are already set; *result points to the level-0 result (type T).
 template <class T>
-eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done);
+eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done, const T** result);
 int vel_final_blocks(int n);
 
 }  // namespace eth

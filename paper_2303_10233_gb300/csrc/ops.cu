@@ -49,6 +49,9 @@ static eth_status apply_t(eth_grid* g, eth_op op, const double* x, double* y) {
     case ETH_OP_K1:
       if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
       return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+    case ETH_OP_K1T:
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
     case ETH_OP_A:
       return run_q2<CT, QF_DIFF | QF_XIN | QF_UOUT>(g, x, nullptr, y, nullptr);
     case ETH_OP_F:
@@ -109,6 +112,40 @@ eth_status op_apply_K(eth_grid* g, bool fp32, bool trans, const double* x, doubl
   if (conv && trans) return run_q2<double, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
   if (conv) return run_q2<double, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
   return run_q2<double, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+}
+
+// ---------------------------------------------------------------------------
+// adjoint gradients: grad_f = M_v D_I l_u ; grad_nu = -(D_I l_u)^T A u
+// ---------------------------------------------------------------------------
+__global__ void k_keep_interior(int n, const double* __restrict__ src, double* __restrict__ dst) {
+  const int N = 2 * n + 1;
+  const size_t nv = (size_t)N * N;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
+    const size_t gg = k < nv ? k : k - nv;
+    const int j = (int)(gg / N), i = (int)(gg - (size_t)j * N);
+    dst[k] = (i == 0 || j == 0 || i == N - 1 || j == N - 1) ? 0.0 : src[k];
+  }
+}
+
+eth_status grad_kernels(eth_grid* g, const double* lu, const double* u, double* grad_f, double* scratch_lm,
+                        double* scratch_au, double* grad_nu) {
+  const size_t nu2 = 2 * (size_t)g->nv;
+  const unsigned nb = cdiv((long)nu2, 256) > 4096 ? 4096 : cdiv((long)nu2, 256);
+  k_keep_interior<<<nb, 256, 0, g->s>>>(g->n, lu, scratch_lm);
+  ETH_CUDA(cudaGetLastError());
+  ETH_TRY((run_q2<double, QF_MASS | QF_XIN | QF_UOUT | QF_NOBC>(g, scratch_lm, nullptr, grad_f, nullptr)));
+  // A u on the full lattice (no Dirichlet treatment), unit viscosity, fused dot with D_I l_u
+  Q2Params<double, double, double> P{};
+  P.n = g->n; P.hx = g->hx; P.hy = g->hy; P.nu = 1.0;
+  P.x = u; P.y = scratch_au;
+  Slot s = make_slot(g, 8, q2_blocks(g->n));
+  P.slot = s; P.slot_off = 0; P.dv = scratch_lm;
+  ETH_CUDA((launch_q2<double, double, double, QF_DIFF | QF_XIN | QF_UOUT | QF_NOBC | QF_DOT, EPI_APPLY>(P, g->s)));
+  ETH_CUDA(cudaMemcpyAsync(&g->sch->dots[8], &g->sc->dots[8], 8, cudaMemcpyDeviceToHost, g->s));
+  ETH_CUDA(cudaStreamSynchronize(g->s));
+  *grad_nu = -g->sch->dots[8];
+  g->launches += 3;
+  return ETH_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -11,4 +11,6 @@ eth_status op_apply(eth_grid* g, eth_op op, bool fp32, const double* x, double* 
 eth_status op_apply_K_dot(eth_grid* g, bool fp32, bool trans, const double* x, double* y, Slot s, const int* done);
 eth_status op_apply_K(eth_grid* g, bool fp32, bool trans, const double* x, double* y, const int* done);
 eth_status assemble_rhs(eth_grid* g, const double* f, const double* ubc);
+eth_status grad_kernels(eth_grid* g, const double* lu, const double* u, double* grad_f, double* scratch_lm,
+                        double* scratch_au, double* grad_nu);
 }  // namespace eth

@@ -37,8 +37,11 @@ enum : int {
   QF_MASS = 512,    // velocity mass term int u phi_i
   QF_NOBC = 1024,   // no Dirichlet masking / identity rows
   QF_SD = 2048,     // streamline diffusion sum_T d_T int (w.grad u)(w.grad v) (coarse levels)
+  QF_SRC_JB = 4096, // x field = omega * dinv * b (first Jacobi sweep from zero), b read from bx
+  QF_SRC_XPC = 8192,// x field = x + P xc (coarse-grid correction prolongated on the fly)
 };
-enum : int { EPI_APPLY = 0, EPI_SMOOTH = 1, EPI_RESID = 2, EPI_SCALE = 3, EPI_BSUB = 4 };
+enum : int { EPI_APPLY = 0, EPI_SMOOTH = 1, EPI_RESID = 2, EPI_SCALE = 3, EPI_BSUB = 4, EPI_JR = 5 };
+// EPI_JR (with QF_SRC_JB): y = b - F x and y2 = x = omega D^{-1} b; bcopy = b (optional).
 // EPI_SCALE: y = dinv * (op x) on the interior, 0 on the boundary.
 // EPI_BSUB:  y = bsrc - (op x) on the interior, bsrc on the boundary.
 
@@ -61,15 +64,119 @@ struct Q2Params {
   const TO* dvp;      // QF_DOT partner of the pressure output
   const TO* bsrc;     // EPI_SMOOTH: boundary rows copy bsrc (else 0); EPI_BSUB: minuend
   const int* done;    // optional early-exit flag
+  const TI* bx;       // QF_SRC_JB: level right-hand side (masked on the boundary)
+  CT* y2;             // EPI_JR: the iterate x
+  CT* bcopy;          // EPI_JR: copy of b (CT), may be null
+  const CT* xc;       // QF_SRC_XPC: coarse-level iterate (level n/2)
 };
+
+// Closed-form element integrals on the unit interval (shape functions as in
+// common.cuh).  Quadratic stiffness / mass: k1d = (1/3)[7 -8 1; -8 16 -8; 1 -8 7],
+// m1d = (1/30)[4 2 -1; 2 16 2; -1 2 4].  Linear-quadratic couplings:
+// c12[c][a] = int N_c L_a', g12[d][b] = int N_d L_b, c0[a] = L_a(1) - L_a(0),
+// g0[b] = int L_b.  On a rectangle hx x hy (local index b*3 + a):
+//   A_e = (hy/hx) k1d (x) m1d + (hx/hy) m1d (x) k1d
+//   B1x_e[(c,d),(a,b)] = -hy c12[c][a] g12[d][b],  B1y_e = -hx g12[c][a] c12[d][b]
+//   B0x_e[(a,b)] = -hy c0[a] g0[b],                B0y_e = -hx g0[a] c0[b]
+__host__ __device__ constexpr double k1d(int a, int b) {
+  return a == b ? (a == 1 ? 16.0 / 3.0 : 7.0 / 3.0) : ((a == 1 || b == 1) ? -8.0 / 3.0 : 1.0 / 3.0);
+}
+__host__ __device__ constexpr double m1d(int a, int b) {
+  return a == b ? (a == 1 ? 16.0 / 30.0 : 4.0 / 30.0) : ((a == 1 || b == 1) ? 2.0 / 30.0 : -1.0 / 30.0);
+}
+__host__ __device__ constexpr double c12(int c, int a) {
+  return c == 0 ? (a == 0 ? -5.0 / 6.0 : (a == 1 ? 2.0 / 3.0 : 1.0 / 6.0)) : (a == 0 ? -1.0 / 6.0 : (a == 1 ? -2.0 / 3.0 : 5.0 / 6.0));
+}
+__host__ __device__ constexpr double g12(int d, int b) {
+  return d == 0 ? (b == 0 ? 1.0 / 6.0 : (b == 1 ? 1.0 / 3.0 : 0.0)) : (b == 0 ? 0.0 : (b == 1 ? 1.0 / 3.0 : 1.0 / 6.0));
+}
+__host__ __device__ constexpr double c0v(int a) { return a == 0 ? -1.0 : (a == 1 ? 0.0 : 1.0); }
+__host__ __device__ constexpr double g0v(int b) { return b == 1 ? 4.0 / 6.0 : 1.0 / 6.0; }
 
 template <class CT, int F>
 __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9], const CT (&P1)[4], CT P0,
                                         CT nu, CT ihx, CT ihy, CT area, CT sdc, CT (&Y)[2][9], CT (&YP1)[4], CT& YP0) {
   constexpr bool CONV = F & QF_CONV, TRANS = F & QF_TRANS, PIN = F & QF_PIN, HP0 = F & QF_P0,
-                 DIFF = F & QF_DIFF, POUT = F & QF_POUT, MASS = F & QF_MASS, SD = F & QF_SD;
+                 DIFF = F & QF_DIFF, POUT = F & QF_POUT, MASS = F & QF_MASS, SD = F & QF_SD, UOUT = F & QF_UOUT;
+  // ---- constant-coefficient parts with the closed-form element matrices (immediates)
+  const CT hx = area * ihy, hy = area * ihx;
+  if (UOUT) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int i = 0; i < 9; ++i) Y[c][i] = 0;
+  }
+  if (UOUT && DIFF) {
+    const CT skm = nu * hy * ihx, smk = nu * hx * ihy;   // nu hy/hx, nu hx/hy
+    if (skm == smk) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          CT acc = 0;
+#pragma unroll
+          for (int j = 0; j < 9; ++j)
+            acc += (CT)(k1d(i % 3, j % 3) * m1d(i / 3, j / 3) + m1d(i % 3, j % 3) * k1d(i / 3, j / 3)) * U[c][j];
+          Y[c][i] = skm * acc;
+        }
+    } else {
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+          CT a1 = 0, a2 = 0;
+#pragma unroll
+          for (int j = 0; j < 9; ++j) {
+            a1 += (CT)(k1d(i % 3, j % 3) * m1d(i / 3, j / 3)) * U[c][j];
+            a2 += (CT)(m1d(i % 3, j % 3) * k1d(i / 3, j / 3)) * U[c][j];
+          }
+          Y[c][i] = skm * a1 + smk * a2;
+        }
+    }
+  }
+  if (UOUT && PIN) {   // B^T p: y_x -= hy (c12 (x) g12)^T p1 + hy c0 g0 p0, y_y with the roles swapped
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int a = i % 3, b = i / 3;
+      CT sx_ = 0, sy_ = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int cc = k & 1, dd = k >> 1;
+        sx_ += (CT)(c12(cc, a) * g12(dd, b)) * P1[k];
+        sy_ += (CT)(g12(cc, a) * c12(dd, b)) * P1[k];
+      }
+      if (HP0) { sx_ += (CT)(c0v(a) * g0v(b)) * P0; sy_ += (CT)(g0v(a) * c0v(b)) * P0; }
+      Y[0][i] -= hy * sx_;
+      Y[1][i] -= hx * sy_;
+    }
+  }
+  if (POUT) {          // B u: yp1 = -hy (c12 (x) g12) u_x - hx (g12 (x) c12) u_y ; yp0 likewise
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int cc = k & 1, dd = k >> 1;
+      CT ax = 0, ay = 0;
+#pragma unroll
+      for (int i = 0; i < 9; ++i) {
+        const int a = i % 3, b = i / 3;
+        ax += (CT)(c12(cc, a) * g12(dd, b)) * U[0][i];
+        ay += (CT)(g12(cc, a) * c12(dd, b)) * U[1][i];
+      }
+      YP1[k] = -(hy * ax + hx * ay);
+    }
+    CT ax = 0, ay = 0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+      const int a = i % 3, b = i / 3;
+      if (c0v(a) * g0v(b) != 0.0) ax += (CT)(c0v(a) * g0v(b)) * U[0][i];
+      if (g0v(a) * c0v(b) != 0.0) ay += (CT)(g0v(a) * c0v(b)) * U[1][i];
+    }
+    YP0 = -(hy * ax + hx * ay);
+  }
+  // ---- wind-dependent / mass terms by sum factorisation at the 3x3 Gauss points
+  constexpr bool SUMF = UOUT && (CONV || MASS || SD);
+  if (!SUMF) return;
   constexpr bool NEEDVAL = (CONV && TRANS) || MASS;
-  constexpr bool NEEDGRAD = DIFF || (CONV && !TRANS) || POUT;
+  constexpr bool NEEDGRAD = (CONV && !TRANS) || SD;
   CT DX[2][9], DY[2][9], VL[2][9];
 #pragma unroll
   for (int c = 0; c < 2; ++c) {
@@ -93,7 +200,7 @@ __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9
       }
   }
   CT WQ[2][9];
-  if (CONV) {
+  if (CONV || SD) {
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       CT T2[3][3];
@@ -119,78 +226,48 @@ __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9
     const CT pe = wn * h / (CT(2) * nu);
     if (pe > CT(1)) delta = sdc * h / (CT(2) * wn) * (CT(1) - CT(1) / pe);
   }
-  CT PQ[9];
-  if (PIN) {
 #pragma unroll
-    for (int qy = 0; qy < 3; ++qy)
-#pragma unroll
-      for (int qx = 0; qx < 3; ++qx) {
-        CT v = NV(qy, 0) * (NV(qx, 0) * P1[0] + NV(qx, 1) * P1[1]) + NV(qy, 1) * (NV(qx, 0) * P1[2] + NV(qx, 1) * P1[3]);
-        if (HP0) v += P0;
-        PQ[qy * 3 + qx] = v;
-      }
-  }
-  if (F & QF_UOUT) {
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      CT GX[9], GY[9], CV[9];
-#pragma unroll
-      for (int qy = 0; qy < 3; ++qy)
-#pragma unroll
-        for (int qx = 0; qx < 3; ++qx) {
-          const int q = qy * 3 + qx;
-          const CT wq = GW(qx) * GW(qy) * area;
-          CT gx = 0, gy = 0, cv = 0;
-          if (DIFF) { gx = nu * DX[c][q]; gy = nu * DY[c][q]; }
-          if (PIN) { if (c == 0) gx -= PQ[q]; else gy -= PQ[q]; }
-          if (CONV && !TRANS) cv = WQ[0][q] * DX[c][q] + WQ[1][q] * DY[c][q];
-          if (SD) { gx += delta * WQ[0][q] * cv; gy += delta * WQ[1][q] * cv; }
-          if (CONV && TRANS) { gx += WQ[0][q] * VL[c][q]; gy += WQ[1][q] * VL[c][q]; }
-          if (MASS) cv += VL[c][q];
-          GX[q] = wq * ihx * gx; GY[q] = wq * ihy * gy; CV[q] = wq * cv;
-        }
-      CT H1[3][3], H2[3][3];   // [qx][b]
-#pragma unroll
-      for (int qx = 0; qx < 3; ++qx)
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          H1[qx][b] = LV(0, b) * GX[qx] + LV(1, b) * GX[3 + qx] + LV(2, b) * GX[6 + qx];
-          H2[qx][b] = LD(0, b) * GY[qx] + LD(1, b) * GY[3 + qx] + LD(2, b) * GY[6 + qx] +
-                      LV(0, b) * CV[qx] + LV(1, b) * CV[3 + qx] + LV(2, b) * CV[6 + qx];
-        }
-#pragma unroll
-      for (int b = 0; b < 3; ++b)
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-          Y[c][b * 3 + a] = LD(0, a) * H1[0][b] + LD(1, a) * H1[1][b] + LD(2, a) * H1[2][b] +
-                            LV(0, a) * H2[0][b] + LV(1, a) * H2[1][b] + LV(2, a) * H2[2][b];
-    }
-  }
-  if (POUT) {
-    CT s[4] = {0, 0, 0, 0};
-    CT s0 = 0;
+  for (int c = 0; c < 2; ++c) {
+    CT GX[9], GY[9], CV[9];
 #pragma unroll
     for (int qy = 0; qy < 3; ++qy)
 #pragma unroll
       for (int qx = 0; qx < 3; ++qx) {
         const int q = qy * 3 + qx;
-        const CT dv = -(GW(qx) * GW(qy) * area) * (DX[0][q] + DY[1][q]);
-        s0 += dv;
+        const CT wq = GW(qx) * GW(qy) * area;
+        CT gx = 0, gy = 0, cv = 0;
+        if ((CONV && !TRANS) || SD) {
+          const CT wgu = WQ[0][q] * DX[c][q] + WQ[1][q] * DY[c][q];
+          if (CONV && !TRANS) cv = wgu;
+          if (SD) { gx += delta * WQ[0][q] * wgu; gy += delta * WQ[1][q] * wgu; }
+        }
+        if (CONV && TRANS) { gx += WQ[0][q] * VL[c][q]; gy += WQ[1][q] * VL[c][q]; }
+        if (MASS) cv += VL[c][q];
+        GX[q] = wq * ihx * gx; GY[q] = wq * ihy * gy; CV[q] = wq * cv;
+      }
+    CT H1[3][3], H2[3][3];   // [qx][b]
 #pragma unroll
-        for (int d = 0; d < 2; ++d)
+    for (int qx = 0; qx < 3; ++qx)
 #pragma unroll
-          for (int cc = 0; cc < 2; ++cc) s[d * 2 + cc] += NV(qy, d) * NV(qx, cc) * dv;
+      for (int b = 0; b < 3; ++b) {
+        H1[qx][b] = LV(0, b) * GX[qx] + LV(1, b) * GX[3 + qx] + LV(2, b) * GX[6 + qx];
+        H2[qx][b] = LD(0, b) * GY[qx] + LD(1, b) * GY[3 + qx] + LD(2, b) * GY[6 + qx] +
+                    LV(0, b) * CV[qx] + LV(1, b) * CV[3 + qx] + LV(2, b) * CV[6 + qx];
       }
 #pragma unroll
-    for (int k = 0; k < 4; ++k) YP1[k] = s[k];
-    YP0 = s0;
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        Y[c][b * 3 + a] += LD(0, a) * H1[0][b] + LD(1, a) * H1[1][b] + LD(2, a) * H1[2][b] +
+                           LV(0, a) * H2[0][b] + LV(1, a) * H2[1][b] + LV(2, a) * H2[2][b];
   }
 }
 
 template <class TI, class TO, class CT, int F, int EPI>
 __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
   constexpr bool CONV = F & QF_CONV, XIN = F & QF_XIN, PIN = F & QF_PIN, HP0 = F & QF_P0,
-                 UOUT = F & QF_UOUT, POUT = F & QF_POUT, DOT = F & QF_DOT, NOBC = F & QF_NOBC;
+                 UOUT = F & QF_UOUT, POUT = F & QF_POUT, DOT = F & QF_DOT, NOBC = F & QF_NOBC,
+                 JB = F & QF_SRC_JB, XPC = F & QF_SRC_XPC;
   if (P.done != nullptr && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sx = reinterpret_cast<CT*>(smem_raw);                 // [2][SQY][SQX]
@@ -206,34 +283,117 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
   const int gi0 = 2 * (ex0 - 1), gj0 = 2 * (ey0 - 1);
   const int tid = threadIdx.x;
 
-  // ---- phase 0: stage inputs (masked velocity, wind, pressure) in shared memory
+  // ---- phase 0: stage inputs (masked velocity, wind, pressure) in shared memory.
+  // All global loads of a thread are issued before any is used (memory-level parallelism).
   if (XIN || CONV) {
-    for (int k = tid; k < SQY * SQX; k += Q2T) {
+    constexpr int NLD = (SQY * SQX + Q2T - 1) / Q2T;
+    TI v0[NLD], v1[NLD];
+    CT w0[NLD], w1[NLD];
+#pragma unroll
+    for (int r = 0; r < NLD; ++r) {
+      const int k = tid + r * Q2T;
       const int lj = k / SQX, li = k - lj * SQX;
       const int i = gi0 + li, j = gj0 + lj;
-      CT v0 = 0, v1 = 0, w0 = 0, w1 = 0;
-      if (i >= 0 && i < N && j >= 0 && j < N) {
+      v0[r] = 0; v1[r] = 0; w0[r] = 0; w1[r] = 0;
+      if (k < SQY * SQX && i >= 0 && i < N && j >= 0 && j < N) {
         const size_t g = (size_t)j * N + i;
         const bool bnd = !NOBC && (i == 0 || j == 0 || i == N - 1 || j == N - 1);
-        if (XIN && !bnd) { v0 = (CT)P.x[g]; v1 = (CT)P.x[g + nv]; }
-        if (CONV) { w0 = P.w[g]; w1 = P.w[g + nv]; }
+        if (XIN && !bnd) {
+          if (JB) { v0[r] = P.bx[g]; v1[r] = P.bx[g + nv]; w0[r] = P.dinv[g]; }
+          else { v0[r] = P.x[g]; v1[r] = P.x[g + nv]; }
+        }
+        if (CONV) { if (JB) w1[r] = P.w[g]; else { w0[r] = P.w[g]; w1[r] = P.w[g + nv]; } }
       }
-      if (XIN) { sx[k] = v0; sx[SQY * SQX + k] = v1; }
-      if (CONV) { sw[k] = w0; sw[SQY * SQX + k] = w1; }
+    }
+#pragma unroll
+    for (int r = 0; r < NLD; ++r) {
+      const int k = tid + r * Q2T;
+      if (k < SQY * SQX) {
+        if (JB) {
+          const CT om = P.omega * w0[r];
+          sx[k] = om * cvt<CT, TI>(v0[r]); sx[SQY * SQX + k] = om * cvt<CT, TI>(v1[r]);
+        } else if (XIN) { sx[k] = cvt<CT, TI>(v0[r]); sx[SQY * SQX + k] = cvt<CT, TI>(v1[r]); }
+        if (CONV && !JB) { sw[k] = w0[r]; sw[SQY * SQX + k] = w1[r]; }
+      }
+    }
+    if (CONV && JB) {   // the wind's second component was not staged above
+      for (int k = tid; k < SQY * SQX; k += Q2T) {
+        const int lj = k / SQX, li = k - lj * SQX;
+        const int i = gi0 + li, j = gj0 + lj;
+        CT a = 0, b = 0;
+        if (i >= 0 && i < N && j >= 0 && j < N) { const size_t g = (size_t)j * N + i; a = P.w[g]; b = P.w[g + nv]; }
+        sw[k] = a; sw[SQY * SQX + k] = b;
+      }
+    }
+    if (XPC) {
+      // coarse lattice (level n/2 has 2*(n/2)+1 = n+1 nodes per direction) covering the fine tile
+      const int Nc = n + 1;
+      const size_t nvc = (size_t)Nc * Nc;
+      const int cI0 = 2 * (gi0 >= 0 ? gi0 / 4 : -1), cJ0 = 2 * (gj0 >= 0 ? gj0 / 4 : -1);
+      constexpr int CXW = (SQX + 3) / 2 + 4, CYW = (SQY + 3) / 2 + 4;
+      CT* sc = eo;   // scratch: eo is unused until phase 1
+      __syncthreads();
+      for (int k = tid; k < CYW * CXW; k += Q2T) {
+        const int lj = k / CXW, li = k - lj * CXW;
+        const int I = cI0 + li, J = cJ0 + lj;
+        CT a = 0, b = 0;
+        if (I >= 0 && I < Nc && J >= 0 && J < Nc) { const size_t c = (size_t)J * Nc + I; a = P.xc[c]; b = P.xc[c + nvc]; }
+        sc[k] = a; sc[CYW * CXW + k] = b;
+      }
+      __syncthreads();
+      for (int k = tid; k < SQY * SQX; k += Q2T) {
+        const int lj = k / SQX, li = k - lj * SQX;
+        const int i = gi0 + li, j = gj0 + lj;
+        if (i <= 0 || j <= 0 || i >= N - 1 || j >= N - 1) continue;   // boundary / outside: no correction
+        int cx[3], cy[3];
+        CT wx[3], wy[3];
+        int nx, ny;
+        if (!(i & 1)) { cx[0] = i >> 1; wx[0] = 1; nx = 1; }
+        else {
+          const int E = i >> 2; nx = 3;
+          cx[0] = 2 * E; cx[1] = 2 * E + 1; cx[2] = 2 * E + 2;
+          if ((i & 3) == 1) { wx[0] = CT(0.375); wx[1] = CT(0.75); wx[2] = CT(-0.125); }
+          else { wx[0] = CT(-0.125); wx[1] = CT(0.75); wx[2] = CT(0.375); }
+        }
+        if (!(j & 1)) { cy[0] = j >> 1; wy[0] = 1; ny = 1; }
+        else {
+          const int E = j >> 2; ny = 3;
+          cy[0] = 2 * E; cy[1] = 2 * E + 1; cy[2] = 2 * E + 2;
+          if ((j & 3) == 1) { wy[0] = CT(0.375); wy[1] = CT(0.75); wy[2] = CT(-0.125); }
+          else { wy[0] = CT(-0.125); wy[1] = CT(0.75); wy[2] = CT(0.375); }
+        }
+        CT a = 0, b = 0;
+        for (int u = 0; u < ny; ++u)
+          for (int v = 0; v < nx; ++v) {
+            const int c = (cy[u] - cJ0) * CXW + (cx[v] - cI0);
+            a += wx[v] * wy[u] * sc[c];
+            b += wx[v] * wy[u] * sc[CYW * CXW + c];
+          }
+        sx[k] += a;
+        sx[SQY * SQX + k] += b;
+      }
     }
   }
   if (PIN) {
-    for (int k = tid; k < SPY * SPX; k += Q2T) {
+    constexpr int NLP = (SPY * SPX + Q2T - 1) / Q2T;
+    TI pv[NLP], p0v = 0;
+#pragma unroll
+    for (int r = 0; r < NLP; ++r) {
+      const int k = tid + r * Q2T;
       const int lj = k / SPX, li = k - lj * SPX;
       const int I = ex0 - 1 + li, J = ey0 - 1 + lj;
-      sp1[k] = (I >= 0 && I <= n && J >= 0 && J <= n) ? (CT)P.p[(size_t)J * (n + 1) + I] : CT(0);
+      pv[r] = (k < SPY * SPX && I >= 0 && I <= n && J >= 0 && J <= n) ? P.p[(size_t)J * (n + 1) + I] : TI(0);
     }
     if (HP0) {
-      for (int k = tid; k < TEY * TEX; k += Q2T) {
-        const int ly = k / TEX, lx = k - ly * TEX;
-        const int ex = ex0 - 1 + lx, ey = ey0 - 1 + ly;
-        sp0[k] = (ex >= 0 && ex < n && ey >= 0 && ey < n) ? (CT)P.p[n1 + (size_t)ey * n + ex] : CT(0);
-      }
+      const int ly = tid / TEX, lx = tid - ly * TEX;
+      const int ex = ex0 - 1 + lx, ey = ey0 - 1 + ly;
+      if (ex >= 0 && ex < n && ey >= 0 && ey < n) p0v = P.p[n1 + (size_t)ey * n + ex];
+      sp0[tid] = cvt<CT, TI>(p0v);
+    }
+#pragma unroll
+    for (int r = 0; r < NLP; ++r) {
+      const int k = tid + r * Q2T;
+      if (k < SPY * SPX) sp1[k] = cvt<CT, TI>(pv[r]);
     }
   }
   __syncthreads();
@@ -282,85 +442,91 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
   __syncthreads();
 
   double dacc = 0.0;
-  // ---- phase 2a: owned velocity nodes gather their element contributions
-  if (UOUT) {
-    const int iend = (ex0 + OEX >= n) ? N : 2 * (ex0 + OEX);
-    const int jend = (ey0 + OEY >= n) ? N : 2 * (ey0 + OEY);
-    const int nli = iend - gi0 - 2, nlj = jend - gj0 - 2;
-    for (int k = tid; k < nli * nlj; k += Q2T) {
-      const int lj = 2 + k / nli, li = 2 + k % nli;
-      int xl[2], xa[2], nx, yl[2], yb[2], ny;
-      if (li & 1) { xl[0] = (li - 1) >> 1; xa[0] = 1; nx = 1; }
-      else { const int m = li >> 1; xl[0] = m - 1; xa[0] = 2; nx = 1; if (m < TEX) { xl[1] = m; xa[1] = 0; nx = 2; } }
-      if (lj & 1) { yl[0] = (lj - 1) >> 1; yb[0] = 1; ny = 1; }
-      else { const int m = lj >> 1; yl[0] = m - 1; yb[0] = 2; ny = 1; if (m < TEY) { yl[1] = m; yb[1] = 0; ny = 2; } }
-      CT s0 = 0, s1 = 0;
-      for (int u = 0; u < ny; ++u)
-        for (int v = 0; v < nx; ++v) {
-          const int t = yl[u] * TEX + xl[v];
-          const int kk = yb[u] * 3 + xa[v];
-          s0 += eo[kk * Q2T + t];
-          s1 += eo[(9 + kk) * Q2T + t];
-        }
-      const int i = gi0 + li, j = gj0 + lj;
+  // ---- phase 2: every owned element (tile-local lx, ly >= 1) gathers the four nodes it
+  // owns (its lower-left vertex, the two adjacent edge midpoints, its centre) plus, on the
+  // last element row / column of the domain, the nodes of the top / right boundary line.
+  {
+    const int lx = tid % TEX, ly = tid / TEX;
+    const int ex = ex0 - 1 + lx, ey = ey0 - 1 + ly;
+    const bool own = lx >= 1 && ly >= 1 && ex < n && ey < n;
+    const int tL = tid - 1, tB = tid - TEX, tLB = tid - TEX - 1;
+    auto E = [&](int a, int b, int t, int c) -> CT { return eo[(c * 9 + b * 3 + a) * Q2T + t]; };
+    auto emit = [&](int i, int j, CT s0, CT s1) {
       const size_t g = (size_t)j * N + i;
       const bool bnd = !NOBC && (i == 0 || j == 0 || i == N - 1 || j == N - 1);
+      const int li = i - gi0, lj = j - gj0;
       TO o0, o1;
       if (EPI == EPI_APPLY) {
         if (bnd) {
           if (XIN) { o0 = (TO)P.x[g]; o1 = (TO)P.x[g + nv]; } else { o0 = 0; o1 = 0; }
-        } else { o0 = (TO)s0; o1 = (TO)s1; }
+        } else { o0 = cvt<TO, CT>(s0); o1 = cvt<TO, CT>(s1); }
       } else if (EPI == EPI_SMOOTH) {
         if (bnd) { if (P.bsrc) { o0 = (TO)P.bsrc[g]; o1 = (TO)P.bsrc[g + nv]; } else { o0 = 0; o1 = 0; } }
         else {
-          const int s = lj * SQX + li;
+          const int sI = lj * SQX + li;
           const CT di = P.omega * P.dinv[g];
-          o0 = (TO)(sx[s] + di * (P.b[g] - s0));
-          o1 = (TO)(sx[SQY * SQX + s] + di * (P.b[g + nv] - s1));
+          o0 = cvt<TO, CT>(sx[sI] + di * (P.b[g] - s0));
+          o1 = cvt<TO, CT>(sx[SQY * SQX + sI] + di * (P.b[g + nv] - s1));
         }
       } else if (EPI == EPI_RESID) {
         if (bnd) { o0 = 0; o1 = 0; } else { o0 = (TO)(P.b[g] - s0); o1 = (TO)(P.b[g + nv] - s1); }
       } else if (EPI == EPI_SCALE) {
         if (bnd) { o0 = 0; o1 = 0; } else { o0 = (TO)(P.dinv[g] * s0); o1 = (TO)(P.dinv[g] * s1); }
-      } else {  // EPI_BSUB
+      } else if (EPI == EPI_BSUB) {
         if (bnd) { o0 = P.bsrc[g]; o1 = P.bsrc[g + nv]; } else { o0 = P.bsrc[g] - (TO)s0; o1 = P.bsrc[g + nv] - (TO)s1; }
+      } else {  // EPI_JR
+        const int sI = lj * SQX + li;
+        if (bnd) {
+          o0 = 0; o1 = 0;
+          P.y2[g] = 0; P.y2[g + nv] = 0;
+          if (P.bcopy) { P.bcopy[g] = 0; P.bcopy[g + nv] = 0; }
+        } else {
+          const CT b0 = cvt<CT, TI>(P.bx[g]), b1 = cvt<CT, TI>(P.bx[g + nv]);
+          o0 = (TO)(b0 - s0); o1 = (TO)(b1 - s1);
+          P.y2[g] = sx[sI]; P.y2[g + nv] = sx[SQY * SQX + sI];
+          if (P.bcopy) { P.bcopy[g] = b0; P.bcopy[g + nv] = b1; }
+        }
       }
       P.y[g] = o0;
       P.y[g + nv] = o1;
-      if (DOT) dacc += (double)o0 * P.dv[g] + (double)o1 * P.dv[g + nv];
-    }
-  }
-  // ---- phase 2b: owned pressure rows (B u)
-  if (POUT) {
-    const int Iend = (ex0 + OEX >= n) ? n + 1 : ex0 + OEX;
-    const int Jend = (ey0 + OEY >= n) ? n + 1 : ey0 + OEY;
-    const int nI = Iend - ex0, nJ = Jend - ey0;
-    for (int k = tid; k < nI * nJ; k += Q2T) {
-      const int LJ = 1 + k / nI, LI = 1 + k % nI;
-      CT s = 0;
-#pragma unroll
-      for (int dd = 0; dd < 2; ++dd) {
-        const int ly = LJ - 1 + dd, d = 1 - dd;     // element below (d=1), above (d=0)
-        if (ly >= TEY) continue;
-#pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-          const int lx = LI - 1 + cc, c = 1 - cc;
-          if (lx >= TEX) continue;
-          s += eo[(18 + d * 2 + c) * Q2T + ly * TEX + lx];
-        }
+      if (DOT) dacc += (double)o0 * (double)P.dv[g] + (double)o1 * (double)P.dv[g + nv];
+    };
+    if (UOUT && own) {
+      const int i0 = 2 * ex, j0 = 2 * ey;
+      const bool lastx = ex == n - 1, lasty = ey == n - 1;
+      // vertex (2ex, 2ey)
+      emit(i0, j0, E(2, 2, tLB, 0) + E(0, 2, tB, 0) + E(2, 0, tL, 0) + E(0, 0, tid, 0),
+                   E(2, 2, tLB, 1) + E(0, 2, tB, 1) + E(2, 0, tL, 1) + E(0, 0, tid, 1));
+      emit(i0 + 1, j0, E(1, 2, tB, 0) + E(1, 0, tid, 0), E(1, 2, tB, 1) + E(1, 0, tid, 1));
+      emit(i0, j0 + 1, E(2, 1, tL, 0) + E(0, 1, tid, 0), E(2, 1, tL, 1) + E(0, 1, tid, 1));
+      emit(i0 + 1, j0 + 1, E(1, 1, tid, 0), E(1, 1, tid, 1));
+      if (lastx) {
+        emit(i0 + 2, j0, E(2, 2, tB, 0) + E(2, 0, tid, 0), E(2, 2, tB, 1) + E(2, 0, tid, 1));
+        emit(i0 + 2, j0 + 1, E(2, 1, tid, 0), E(2, 1, tid, 1));
       }
-      const size_t gp = (size_t)(ey0 - 1 + LJ) * (n + 1) + (ex0 - 1 + LI);
-      P.yp[gp] = (TO)s;
-      if (DOT) dacc += (double)(TO)s * P.dvp[gp];
+      if (lasty) {
+        emit(i0, j0 + 2, E(2, 2, tL, 0) + E(0, 2, tid, 0), E(2, 2, tL, 1) + E(0, 2, tid, 1));
+        emit(i0 + 1, j0 + 2, E(1, 2, tid, 0), E(1, 2, tid, 1));
+      }
+      if (lastx && lasty) emit(i0 + 2, j0 + 2, E(2, 2, tid, 0), E(2, 2, tid, 1));
     }
-    if (HP0) {
-      const int nEx = min(OEX, n - ex0), nEy = min(OEY, n - ey0);
-      for (int k = tid; k < nEx * nEy; k += Q2T) {
-        const int ly = 1 + k / nEx, lx = 1 + k % nEx;
-        const size_t ge = (size_t)n1 + (size_t)(ey0 - 1 + ly) * n + (ex0 - 1 + lx);
-        const CT s = eo[22 * Q2T + ly * TEX + lx];
-        P.yp[ge] = (TO)s;
-        if (DOT) dacc += (double)(TO)s * P.dvp[ge];
+    if (POUT && own) {
+      auto Q = [&](int cc, int dd, int t) -> CT { return eo[(18 + dd * 2 + cc) * Q2T + t]; };
+      auto pemit = [&](int I, int J, CT v) {
+        const size_t gp = (size_t)J * (n + 1) + I;
+        const TO so = cvt<TO, CT>(v);
+        P.yp[gp] = so;
+        if (DOT) dacc += (double)so * (double)P.dvp[gp];
+      };
+      pemit(ex, ey, Q(1, 1, tLB) + Q(0, 1, tB) + Q(1, 0, tL) + Q(0, 0, tid));
+      if (ex == n - 1) pemit(ex + 1, ey, Q(1, 1, tB) + Q(1, 0, tid));
+      if (ey == n - 1) pemit(ex, ey + 1, Q(1, 1, tL) + Q(0, 1, tid));
+      if (ex == n - 1 && ey == n - 1) pemit(ex + 1, ey + 1, Q(1, 1, tid));
+      if (HP0) {
+        const size_t ge = (size_t)n1 + (size_t)ey * n + ex;
+        const TO so = cvt<TO, CT>(eo[22 * Q2T + tid]);
+        P.yp[ge] = so;
+        if (DOT) dacc += (double)so * (double)P.dvp[ge];
       }
     }
   }

@@ -15,7 +15,7 @@ static void work_free(void* p) {
   Work* w = (Work*)p;
   if (!w) return;
   gmres_free(w);
-  mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
+  mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd); mg_free(w->vft); mg_free(w->vdt);
   cudaFree(w->x); cudaFree(w->d); cudaFree(w->r); cudaFree(w->Kz); cudaFree(w->bp);
   for (int k = 0; k < 2; ++k) { cudaFree(w->V[k]); cudaFree(w->Z[k]); cudaFree(w->W[k]); }
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
@@ -37,7 +37,7 @@ void solver_free(eth_grid* g) {
 eth_status solver_coefficients_changed(eth_grid* g) {
   Work* w = (Work*)g->ws;
   if (!w) return ETH_OK;
-  mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
+  mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd); mg_free(w->vft); mg_free(w->vdt);
   if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; w->gkey = -1; }
   gmres_free(w);
   return ETH_OK;
@@ -64,7 +64,7 @@ eth_status work_get(eth_grid* g, Work** out) {
 
 int vblocks(size_t m) {
   size_t b = (m + 255) / 256;
-  if (b > 152 * 8) b = 152 * 8;
+  if (b > 152 * 4) b = 152 * 4;
   return (int)(b < 1 ? 1 : b);
 }
 
@@ -174,7 +174,7 @@ __global__ void k_mq_t(int n, const double* __restrict__ vp, const Scalars* __re
         s += vp[n1 + (size_t)ey * n + ex] + beta;
       }
     }
-    const T t = (T)(vp[node] - beta - 0.25 * s);
+    const T t = cvt<T, double>(vp[node] - beta - 0.25 * s);
     b[node] = t;
     x[node] = omega * dinv[node] * t;
   }
@@ -235,13 +235,14 @@ eth_status precond_pressure(eth_grid* g, Hier<T>& Q, const double* vp, double* z
   g->s = s;
   k_mq_t<T><<<vblocks(g->n1), 256, 0, s>>>(g->n, vp, g->sc, L0.b, L0.x, L0.dinv, (T)Q.omega, done);
   ETH_CUDA(cudaGetLastError());
-  eth_status st = vcycle_q1_from<T>(g, Q, 1, 1, done);
+  const T* zt = nullptr;
+  eth_status st = vcycle_q1_from<T>(g, Q, 1, 1, done, &zt);
   if (st != ETH_OK) { g->s = keep; return st; }
   const int nb = mq_blocks(g);
   Slot sm = slot_of(g, SL_MQ, nb, FIN_MQ);
-  k_mq_sums<T><<<nb, 256, 0, s>>>(g->n, L0.x, vp, g->hx * g->hy, sm, done);
+  k_mq_sums<T><<<nb, 256, 0, s>>>(g->n, zt, vp, g->hx * g->hy, sm, done);
   ETH_CUDA(cudaGetLastError());
-  k_mq_out<T><<<nb, 256, 0, s>>>(g->n, L0.x, vp, zp, g->hx * g->hy, g->sc, gsl, goff, done);
+  k_mq_out<T><<<nb, 256, 0, s>>>(g->n, zt, vp, zp, g->hx * g->hy, g->sc, gsl, goff, done);
   ETH_CUDA(cudaGetLastError());
   g->launches += 3;
   g->s = keep;
@@ -252,6 +253,10 @@ template <>
 Hier<float>& vel_hier<float>(Work* w) { return w->vf; }
 template <>
 Hier<double>& vel_hier<double>(Work* w) { return w->vd; }
+template <>
+Hier<float>& vel_hier_t<float>(Work* w) { return w->vft; }
+template <>
+Hier<double>& vel_hier_t<double>(Work* w) { return w->vdt; }
 template <>
 Hier<float>& q1_hier<float>(Work* w) { return w->qf; }
 template <>
@@ -367,13 +372,17 @@ template <class T>
 eth_status ensure_hier(eth_grid* g, Work* w, const eth_opts* o) {
   const int nmin = std::max(2, o->mg_min_n);
   if (w->nmin_built != nmin) {
-    mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd);
+    mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd); mg_free(w->vft); mg_free(w->vdt);
     if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; w->gkey = -1; }
     w->nmin_built = nmin;
   }
   Hier<T>& V = vel_hier<T>(w);
   Hier<T>& Q = q1_hier<T>(w);
-  if (!V.built) ETH_TRY(mg_build_vel<T>(g, V, nmin, 0.0));
+  if (!V.built) ETH_TRY(mg_build_vel<T>(g, V, nmin, g->kind == ETH_OSEEN ? 0.5 : 0.0, false));
+  if (g->kind == ETH_OSEEN && w->need_adj) {
+    Hier<T>& Vt = vel_hier_t<T>(w);
+    if (!Vt.built) ETH_TRY(mg_build_vel<T>(g, Vt, nmin, 0.5, true));
+  }
   if (!Q.built) ETH_TRY(mg_build_q1<T>(g, Q, nmin));
   return ETH_OK;
 }
@@ -404,11 +413,11 @@ eth_status canonicalize(eth_grid* g, double* x) {
 }
 
 template <class T>
-static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st) {
+static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, const double* bsrc) {
   const size_t nt = g->nt;
   const bool fp32 = o->precision == ETH_MIXED;
   // consistent right-hand side: b with its e1 / e0 components removed
-  ETH_CUDA(cudaMemcpyAsync(w->bp, g->b, nt * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaMemcpyAsync(w->bp, bsrc, nt * 8, cudaMemcpyDeviceToDevice, g->s));
   ETH_TRY(canonicalize(g, w->bp));
   ETH_CUDA(cudaMemcpyAsync(g->sch->dots, g->sc->dots, sizeof(g->sc->dots), cudaMemcpyDeviceToHost, g->s));
   double bb = 0.0;
@@ -469,6 +478,10 @@ static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stat
 template eth_status ensure_hier<float>(eth_grid*, Work*, const eth_opts*);
 template eth_status ensure_hier<double>(eth_grid*, Work*, const eth_opts*);
 
+eth_status adjoint_gradients(eth_grid* g, Work* w, const double* lu, const double* u, double* grad_f, double* grad_nu) {
+  return grad_kernels(g, lu, u, grad_f, w->r, w->Kz, grad_nu);
+}
+
 }  // namespace eth
 
 using namespace eth;
@@ -497,8 +510,8 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   ETH_CUDA(cudaGetLastError());
   g->launches++;
   eth_status r;
-  if (g->kind == ETH_OSEEN) r = oseen_solve(g, w, &o, &st, false);
-  else r = o.precision == ETH_MIXED ? stokes_solve<float>(g, w, &o, &st) : stokes_solve<double>(g, w, &o, &st);
+  if (g->kind == ETH_OSEEN) r = oseen_solve(g, w, &o, &st, false, g->b);
+  else r = o.precision == ETH_MIXED ? stokes_solve<float>(g, w, &o, &st, g->b) : stokes_solve<double>(g, w, &o, &st, g->b);
   if (r == ETH_ECUDA || r == ETH_ENOMEM || r == ETH_EINVAL) return r;
   ETH_CUDA(cudaMemcpyAsync(u, w->x, nu2 * 8, cudaMemcpyDeviceToDevice, g->s));
   ETH_CUDA(cudaMemcpyAsync(p, w->x + nu2, (size_t)(g->n1 + g->n0) * 8, cudaMemcpyDeviceToDevice, g->s));
@@ -535,11 +548,56 @@ eth_status eth_solve_host(eth_grid* g, const eth_opts* opts, const double* f, co
   return r;
 }
 
-eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* o, const double* ru, const double* rp, double* lu, double* lp, eth_stats* st) {
-  (void)g; (void)o; (void)ru; (void)rp; (void)lu; (void)lp; (void)st;
-  set_error("eth_solve_adjoint: not available in this build");
-  return ETH_EINVAL;
+eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru, const double* rp, double* lu, double* lp,
+                             eth_stats* stats) {
+  if (!g || !ru || !rp || !lu || !lp) { set_error("eth_solve_adjoint: NULL argument"); return ETH_EINVAL; }
+  if (!g->has_coef) { set_error("eth_solve_adjoint: call eth_set_coefficients first"); return ETH_EINVAL; }
+  eth_opts o;
+  if (opts) o = *opts; else eth_default_opts(&o);
+  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1) { set_error("eth_solve_adjoint: bad options"); return ETH_EINVAL; }
+  eth_stats st;
+  std::memset(&st, 0, sizeof(st));
+  Work* w;
+  ETH_TRY(work_get(g, &w));
+  StreamSwap guard(g, w);
+  w->need_adj = true;
+  if (o.precision == ETH_MIXED) ETH_TRY(ensure_hier<float>(g, w, &o)); else ETH_TRY(ensure_hier<double>(g, w, &o));
+  const long l0 = g->launches;
+  ETH_CUDA(cudaEventRecord(w->t0, g->s));
+  const size_t nu2 = 2 * (size_t)g->nv, np = (size_t)g->n1 + g->n0;
+  // right-hand side [r_u; r_p] (boundary rows of K^T are identity rows: l_B = r_B)
+  ETH_CUDA(cudaMemcpyAsync(w->d, ru, nu2 * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaMemcpyAsync(w->d + nu2, rp, np * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaMemsetAsync(w->x, 0, (size_t)g->nt * 8, g->s));
+  k_set_boundary<<<vblocks(nu2), 256, 0, g->s>>>(g->n, w->x, w->d);
+  ETH_CUDA(cudaGetLastError());
+  ETH_CUDA(cudaMemcpyAsync(w->Kz, w->d, (size_t)g->nt * 8, cudaMemcpyDeviceToDevice, g->s));
+  eth_status r;
+  if (g->kind == ETH_OSEEN) r = oseen_solve(g, w, &o, &st, true, w->Kz);
+  else r = o.precision == ETH_MIXED ? stokes_solve<float>(g, w, &o, &st, w->Kz) : stokes_solve<double>(g, w, &o, &st, w->Kz);
+  if (r == ETH_ECUDA || r == ETH_ENOMEM || r == ETH_EINVAL) return r;
+  ETH_CUDA(cudaMemcpyAsync(lu, w->x, nu2 * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaMemcpyAsync(lp, w->x + nu2, np * 8, cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaEventRecord(w->t1, g->s));
+  ETH_CUDA(cudaEventSynchronize(w->t1));
+  float ms = 0.f;
+  ETH_CUDA(cudaEventElapsedTime(&ms, w->t0, w->t1));
+  st.seconds = ms * 1e-3;
+  st.status = r;
+  st.kernel_launches = (int)(g->launches - l0);
+  if (stats) *stats = st;
+  return r;
 }
+
+eth_status eth_adjoint_gradients(eth_grid* g, const double* lu, const double* u, double* grad_f, double* grad_nu) {
+  if (!g || !lu || !u || !grad_f || !grad_nu) { set_error("eth_adjoint_gradients: NULL argument"); return ETH_EINVAL; }
+  Work* w;
+  ETH_TRY(work_get(g, &w));
+  StreamSwap guard(g, w);
+  ETH_TRY(adjoint_gradients(g, w, lu, u, grad_f, grad_nu));
+  return ETH_OK;
+}
+
 eth_status eth_batch_create(int count, eth_grid* const* grids, eth_batch** out) {
   (void)count; (void)grids;
   if (out) *out = nullptr;

@@ -10,8 +10,9 @@ enum : int { SL_DELTA = 0, SL_VSUM = 1, SL_GAMMA = 2, SL_MQ = 3, SL_DONE = 4, SL
 // Solver workspace owned by a handle (created on the first solve).
 struct GMRESWork;
 struct Work {
-  Hier<float> vf, qf;
-  Hier<double> vd, qd;
+  Hier<float> vf, qf, vft;     // velocity (F), Q1 Laplacian, velocity (F^T) hierarchies
+  Hier<double> vd, qd, vdt;
+  bool need_adj = false;       // build the F^T hierarchy (adjoint solves)
   double *x = nullptr, *d = nullptr, *r = nullptr, *Kz = nullptr, *bp = nullptr;
   double *V[2] = {nullptr, nullptr}, *Z[2] = {nullptr, nullptr}, *W[2] = {nullptr, nullptr};
   cudaStream_t s2 = nullptr;   // second branch (pressure block)
@@ -54,8 +55,11 @@ template <class T>
 Hier<T>& vel_hier(Work* w);
 template <class T>
 Hier<T>& q1_hier(Work* w);
+template <class T>
+Hier<T>& vel_hier_t(Work* w);
+eth_status adjoint_gradients(eth_grid* g, Work* w, const double* lu, const double* u, double* grad_f, double* grad_nu);
 void gmres_free(Work* w);
-eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint);
+eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* b);
 
 // Runs the solver body on the handle's internal stream (capturable even when
 // the user stream is the legacy default stream), ordered after and before the

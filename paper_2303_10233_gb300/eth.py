@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libeth.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "eth.h")
 
 STOKES, OSEEN = 0, 1
-OPS = {"K": 0, "KT": 1, "A": 2, "F": 3, "B": 4, "BT": 5, "MQ": 6, "MV": 7, "K1": 8}
+OPS = {"K": 0, "KT": 1, "A": 2, "F": 3, "B": 4, "BT": 5, "MQ": 6, "MV": 7, "K1": 8, "K1T": 9}
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "EBREAKDOWN",
           6: "EINCONSISTENT", 7: "ETIMEOUT", 8: "ENAN"}
 
@@ -76,6 +76,7 @@ def load(path=LIB_PATH):
         "eth_solve_host": (i, [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Stats)]),
         "eth_solve_adjoint": (i, [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Stats)]),
         "eth_apply": (i, [vp, i, i, vp, vp]),
+        "eth_adjoint_gradients": (i, [vp, vp, vp, vp, ctypes.POINTER(d)]),
         "eth_batch_create": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "eth_batch_solve": (i, [vp, ctypes.POINTER(Opts), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)]),
         "eth_batch_destroy": (None, [vp]),
@@ -173,7 +174,7 @@ class Grid:
     def apply(self, op, x, fp32=False):
         out = {"K": self.nt, "KT": self.nt, "A": 2 * self.nv, "F": 2 * self.nv, "MV": 2 * self.nv,
                "B": self.n1 + self.n0, "BT": 2 * self.nv, "MQ": self.n1 + self.n0,
-               "K1": 2 * self.nv + self.n1}[op]
+               "K1": 2 * self.nv + self.n1, "K1T": 2 * self.nv + self.n1}[op]
         y = self._zeros(out)
         _check(load().eth_apply(self.h, OPS[op], int(bool(fp32)), _ptr(x), _ptr(y)))
         return y
@@ -219,6 +220,14 @@ class Grid:
         if rc not in (0, 4):
             _check(rc)
         return lu, lp, st.as_dict()
+
+
+    def adjoint_gradients(self, lu, u):
+        """(grad_f, grad_nu) of J = ||u - u_t||^2 from the adjoint velocity lu."""
+        gf = self._zeros(2 * self.nv)
+        gn = ctypes.c_double()
+        _check(load().eth_adjoint_gradients(self.h, _ptr(lu), _ptr(u), _ptr(gf), ctypes.byref(gn)))
+        return gf, gn.value
 
 
 def problem(w, device=None):
