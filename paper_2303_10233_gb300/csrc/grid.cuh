@@ -63,3 +63,8 @@ struct eth_grid {
   void (*ws_free)(void*) = nullptr;
   long launches = 0;
 };
+
+struct eth_batch {
+  std::vector<eth_grid*> grids;
+  int workers = 0;   // host workers (0: min(count, 16))
+};

@@ -3,6 +3,9 @@
 // Sec. 2.2: the M_Q solve keeps z orthogonal to k), FP64 iterative refinement
 // around mixed-precision inner solves, and the public solve entry points.
 #include <algorithm>
+#include <atomic>
+#include <thread>
+#include <vector>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -599,15 +602,54 @@ eth_status eth_adjoint_gradients(eth_grid* g, const double* lu, const double* u,
 }
 
 eth_status eth_batch_create(int count, eth_grid* const* grids, eth_batch** out) {
-  (void)count; (void)grids;
-  if (out) *out = nullptr;
-  set_error("eth_batch_create: not available in this build");
-  return ETH_EINVAL;
+  if (!out) { set_error("eth_batch_create: out is NULL"); return ETH_EINVAL; }
+  *out = nullptr;
+  if (count < 1 || !grids) { set_error("eth_batch_create: empty batch"); return ETH_EINVAL; }
+  for (int i = 0; i < count; ++i)
+    if (!grids[i]) { set_error("eth_batch_create: grid %d is NULL", i); return ETH_EINVAL; }
+  eth_batch* b = new eth_batch();
+  b->grids.assign(grids, grids + count);
+  *out = b;
+  return ETH_OK;
 }
-eth_status eth_batch_solve(eth_batch* b, const eth_opts* o, double* const* u, double* const* p, eth_stats* st) {
-  (void)b; (void)o; (void)u; (void)p; (void)st;
-  set_error("eth_batch_solve: not available in this build");
-  return ETH_EINVAL;
+
+// Independent instances run concurrently: one host worker per instance slot
+// drives that instance's captured-graph solve on its own internal streams, so
+// the GPU overlaps the instances' kernels.  Instances are handed out largest
+// first (cost ~ N_t) to balance the workers.
+eth_status eth_batch_solve(eth_batch* b, const eth_opts* opts, double* const* u, double* const* p, eth_stats* stats) {
+  if (!b || !u || !p) { set_error("eth_batch_solve: NULL argument"); return ETH_EINVAL; }
+  const int count = (int)b->grids.size();
+  std::vector<int> order(count);
+  for (int i = 0; i < count; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int c) { return b->grids[a]->nt > b->grids[c]->nt; });
+  std::vector<eth_status> st(count, ETH_OK);
+  std::vector<eth_stats> ss(count);
+  std::atomic<int> next{0};
+  const int nw = std::max(1, std::min(count, b->workers > 0 ? b->workers : 16));
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    while (true) {
+      const int k = next.fetch_add(1);
+      if (k >= count) break;
+      const int i = order[k];
+      std::memset(&ss[i], 0, sizeof(eth_stats));
+      st[i] = eth_solve(b->grids[i], opts, u[i], p[i], &ss[i]);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 0; t < nw; ++t) th.emplace_back(worker);
+  for (auto& t : th) t.join();
+  eth_status r = ETH_OK;
+  for (int i = 0; i < count; ++i) {
+    if (stats) stats[i] = ss[i];
+    if (st[i] != ETH_OK && r == ETH_OK) r = st[i];
+  }
+  if (r != ETH_OK) set_error("eth_batch_solve: at least one instance returned %s", eth_status_string(r));
+  return r;
 }
-void eth_batch_destroy(eth_batch* b) { (void)b; }
+
+void eth_batch_destroy(eth_batch* b) { delete b; }
 }

@@ -230,6 +230,38 @@ class Grid:
         return gf, gn.value
 
 
+class Batch:
+    """Concurrent solves of independent instances (wraps eth_batch)."""
+
+    def __init__(self, grids):
+        self.grids = list(grids)
+        arr = (ctypes.c_void_p * len(self.grids))(*[g.h.value for g in self.grids])
+        h = ctypes.c_void_p()
+        _check(load().eth_batch_create(len(self.grids), arr, ctypes.byref(h)))
+        self.h = h
+
+    def solve(self, **opts):
+        us = [g._zeros(2 * g.nv) for g in self.grids]
+        ps = [g._zeros(g.n1 + g.n0) for g in self.grids]
+        ua = (ctypes.c_void_p * len(us))(*[t.data_ptr() for t in us])
+        pa = (ctypes.c_void_p * len(ps))(*[t.data_ptr() for t in ps])
+        st = (Stats * len(us))()
+        o = make_opts(**opts)
+        rc = load().eth_batch_solve(self.h, ctypes.byref(o), ua, pa, st)
+        return us, ps, [s.as_dict() for s in st], rc
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().eth_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def problem(w, device=None):
     """Grid with coefficients and right-hand side from a workloads dict."""
     import torch
