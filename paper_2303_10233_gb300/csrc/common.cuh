@@ -93,6 +93,8 @@ struct Slot {
   int total;           // number of partials expected
   int op;              // finisher run by the last block (FIN_*)
   Scalars* sc;         // scalar state the finisher updates
+  int base;            // inner-PCG state block (FIN_PCG_*)
+  int flag;            // inner-PCG done flag index (FIN_PCG_*)
 };
 
 __device__ __forceinline__ double warp_sum(double v) {

@@ -269,26 +269,21 @@ __global__ void k_q1_mass_diag(int n, double hx, double hy, T* __restrict__ d) {
 
 // Chebyshev step on the Q1 mass: x += d; r -= Q d; d' = c1 d + c2 D^{-1} r
 template <class T>
-__global__ void k_cheb_step(int n, T area, const T* __restrict__ d, T* __restrict__ r, T* __restrict__ x, T* __restrict__ dn,
+__global__ void k_cheb_step(int n, T area, const T* __restrict__ d_in, T* __restrict__ r, T* __restrict__ x, T* __restrict__ dn,
                             const T* __restrict__ dinv, T c1, T c2, const int* done) {
+  const T* d = d_in;
   if (done && *done) return;
   const int M = n + 1;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < M * M; node += gridDim.x * blockDim.x) {
     const int J = node / M, I = node - J * M;
     T q = 0;
-    for (int ey = J - 1; ey <= J; ++ey) {
-      if (ey < 0 || ey >= n) continue;
-      const int dd0 = J - ey;
-      for (int ex = I - 1; ex <= I; ++ex) {
-        if (ex < 0 || ex >= n) continue;
-        const int cc0 = I - ex;
-        for (int dd = 0; dd < 2; ++dd)
-          for (int cc = 0; cc < 2; ++cc) {
-            const T m = (T)((cc == cc0 ? 1.0 / 3.0 : 1.0 / 6.0) * (dd == dd0 ? 1.0 / 3.0 : 1.0 / 6.0));
-            q += area * m * d[(size_t)(ey + dd) * M + ex + cc];
-          }
-      }
-    }
+    Q1_FOR_ELEMENTS(n, I, J, {
+#pragma unroll
+      for (int dd = 0; dd < 2; ++dd)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc)
+          q += area * (T)(q1m(c, cc) * q1m(d, dd)) * d_in[(size_t)(ey + dd) * M + ex + cc];
+    })
     const T rn = r[node] - q;
     r[node] = rn;
     x[node] += d[node];
@@ -332,7 +327,8 @@ template <class T>
 __global__ void k_pcg_xr(int m, const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
                          const GScalars* gs, const int* done) {
   if (done && *done) return;
-  const T a = (T)(gs->pcg[0] / gs->pcg[1]);
+  const double pap = gs->pcg[1];
+  const T a = (T)(pap != 0.0 ? gs->pcg[0] / pap : 0.0);   // zero right-hand side: stay at zero
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
     x[k] += a * p[k];
     r[k] -= a * q[k];
@@ -343,7 +339,7 @@ __global__ void k_pcg_xr(int m, const T* __restrict__ p, const T* __restrict__ q
 template <class T>
 __global__ void k_pcg_p(int m, const T* __restrict__ z, T* __restrict__ p, GScalars* gs, const int* done) {
   if (done && *done) return;
-  const T bt = (T)(gs->pcg[2] / gs->pcg[0]);
+  const T bt = (T)(gs->pcg[0] != 0.0 ? gs->pcg[2] / gs->pcg[0] : 0.0);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) p[k] = z[k] + bt * p[k];
   __syncthreads();
 }
@@ -734,7 +730,7 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
   ETH_TRY(gmres_run<T>(g, w, o, 2, adj, b, w->x, nt, eta * nb2, o->maxit - its1, &its2, &res2, &s2));
   ETH_TRY(canonicalize(g, w->x));
   double rr;
-  ETH_TRY(true_residual(g, w, b, &rr));
+  ETH_TRY(true_residual(g, w, b, &rr, adj));
   st->iters_stage1 = its1;
   st->iters_stage2 = its2;
   st->iters_total = its1 + its2;

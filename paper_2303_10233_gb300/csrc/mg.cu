@@ -86,12 +86,22 @@ __global__ void k_q2_jacobi0(int n, T omega, const T* __restrict__ dinv, const T
   }
 }
 
-// 1D Q2 restriction weights from coarse index I: fine offsets and weights.
-__device__ __forceinline__ int q2_rweights(int I, int* off, float* wt) {
-  if (I & 1) { off[0] = -1; wt[0] = 0.75f; off[1] = 0; wt[1] = 1.f; off[2] = 1; wt[2] = 0.75f; return 3; }
-  off[0] = -3; wt[0] = -0.125f; off[1] = -1; wt[1] = 0.375f; off[2] = 0; wt[2] = 1.f;
-  off[3] = 1; wt[3] = 0.375f; off[4] = 3; wt[4] = -0.125f;
-  return 5;
+// 1D Q2 restriction weight of the fine node at offset o in [-3, 3] from 2I
+// (coarse midpoint I odd: 3/4, 1, 3/4 on o = -1, 0, 1; coarse vertex I even:
+// -1/8, 3/8, 1, 3/8, -1/8 on o = -3, -1, 0, 1, 3; every other offset 0).
+__device__ __forceinline__ float q2_rw(int odd, int o) {
+  if (o == 0) return 1.f;
+  if (odd) return (o == -1 || o == 1) ? 0.75f : 0.f;
+  return (o == -1 || o == 1) ? 0.375f : ((o == -3 || o == 3) ? -0.125f : 0.f);
+}
+// 1D Q2 prolongation to fine index i: coarse base index and three weights
+// (even i: injection; i = 4E+1: 3/8, 3/4, -1/8; i = 4E+3: -1/8, 3/4, 3/8).
+__device__ __forceinline__ int q2_pw(int i, float& w0, float& w1, float& w2) {
+  if (!(i & 1)) { w0 = 1.f; w1 = 0.f; w2 = 0.f; return i >> 1; }
+  const int E = i >> 2;
+  if ((i & 3) == 1) { w0 = 0.375f; w1 = 0.75f; w2 = -0.125f; }
+  else { w0 = -0.125f; w1 = 0.75f; w2 = 0.375f; }
+  return 2 * E;
 }
 
 template <class T>
@@ -102,33 +112,28 @@ __global__ void k_q2_restrict(int nc, const T* __restrict__ rf, T* __restrict__ 
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Nc * Nc; node += gridDim.x * blockDim.x) {
     const int J = node / Nc, I = node - J * Nc;
     if (I == 0 || J == 0 || I == Nc - 1 || J == Nc - 1) { bc[node] = 0; bc[node + nvc] = 0; continue; }
-    int ox[5], oy[5];
-    float wx[5], wy[5];
-    const int nx = q2_rweights(I, ox, wx), ny = q2_rweights(J, oy, wy);
+    const int ox = I & 1, oy = J & 1;
     T s0 = 0, s1 = 0;
-    for (int u = 0; u < ny; ++u) {
-      const size_t row = (size_t)(2 * J + oy[u]) * Nf;
+#pragma unroll
+    for (int u = -3; u <= 3; ++u) {
+      const float wyv = q2_rw(oy, u);
+      if (wyv == 0.f) continue;
+      const size_t row = (size_t)(2 * J + u) * Nf;
       T t0 = 0, t1 = 0;
-      for (int v = 0; v < nx; ++v) {
-        const size_t f = row + 2 * I + ox[v];
-        t0 += (T)wx[v] * rf[f];
-        t1 += (T)wx[v] * rf[f + nvf];
+#pragma unroll
+      for (int v = -3; v <= 3; ++v) {
+        const float wxv = q2_rw(ox, v);
+        if (wxv == 0.f) continue;
+        const size_t f = row + 2 * I + v;
+        t0 += (T)wxv * rf[f];
+        t1 += (T)wxv * rf[f + nvf];
       }
-      s0 += (T)wy[u] * t0;
-      s1 += (T)wy[u] * t1;
+      s0 += (T)wyv * t0;
+      s1 += (T)wyv * t1;
     }
     bc[node] = s0;
     bc[node + nvc] = s1;
   }
-}
-
-// 1D Q2 prolongation weights to fine index i: coarse indices and weights.
-__device__ __forceinline__ int q2_pweights(int i, int* c, float* wt) {
-  if (!(i & 1)) { c[0] = i >> 1; wt[0] = 1.f; return 1; }
-  const int E = i >> 2;
-  if ((i & 3) == 1) { c[0] = 2 * E; wt[0] = 0.375f; c[1] = 2 * E + 1; wt[1] = 0.75f; c[2] = 2 * E + 2; wt[2] = -0.125f; }
-  else { c[0] = 2 * E; wt[0] = -0.125f; c[1] = 2 * E + 1; wt[1] = 0.75f; c[2] = 2 * E + 2; wt[2] = 0.375f; }
-  return 3;
 }
 
 template <class T>
@@ -139,13 +144,15 @@ __global__ void k_q2_prolong_add(int nc, const T* __restrict__ xc, T* __restrict
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Nf * Nf; node += gridDim.x * blockDim.x) {
     const int j = node / Nf, i = node - j * Nf;
     if (i == 0 || j == 0 || i == Nf - 1 || j == Nf - 1) continue;
-    int cx[3], cy[3];
     float wx[3], wy[3];
-    const int nx = q2_pweights(i, cx, wx), ny = q2_pweights(j, cy, wy);
+    const int cx = q2_pw(i, wx[0], wx[1], wx[2]), cy = q2_pw(j, wy[0], wy[1], wy[2]);
     T s0 = 0, s1 = 0;
-    for (int u = 0; u < ny; ++u)
-      for (int v = 0; v < nx; ++v) {
-        const size_t c = (size_t)cy[u] * Nc + cx[v];
+#pragma unroll
+    for (int u = 0; u < 3; ++u)
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        if (wx[v] == 0.f || wy[u] == 0.f) continue;
+        const size_t c = (size_t)(cy + u) * Nc + cx + v;
         const T f = (T)(wx[v] * wy[u]);
         s0 += f * xc[c];
         s1 += f * xc[c + nvc];
@@ -580,16 +587,21 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
       const int J = node / Nc, I = node - J * Nc;
       T s0 = 0, s1 = 0;
       if (!(I == 0 || J == 0 || I == Nc - 1 || J == Nc - 1)) {
-        int ox[5], oy[5];
-        float wx[5], wy[5];
-        const int nx = q2_rweights(I, ox, wx), ny = q2_rweights(J, oy, wy);
-        for (int u = 0; u < ny; ++u)
-          for (int v = 0; v < nx; ++v) {
-            const int f = (2 * J + oy[u]) * N + 2 * I + ox[v];
-            const T c = (T)(wx[v] * wy[u]);
-            s0 += c * R[l][f];
-            s1 += c * R[l][f + nv];
+        const int ox = I & 1, oy = J & 1;
+#pragma unroll
+        for (int u = -3; u <= 3; ++u) {
+          const float wyv = q2_rw(oy, u);
+          if (wyv == 0.f) continue;
+#pragma unroll
+          for (int v = -3; v <= 3; ++v) {
+            const float wxv = q2_rw(ox, v);
+            if (wxv == 0.f) continue;
+            const int f = (2 * J + u) * N + 2 * I + v;
+            const T cf = (T)(wxv * wyv);
+            s0 += cf * R[l][f];
+            s1 += cf * R[l][f + nv];
           }
+        }
       }
       B[l + 1][node] = s0;
       B[l + 1][node + nvc] = s1;
@@ -614,13 +626,15 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
     for (int node = threadIdx.x; node < nv; node += blockDim.x) {
       const int j = node / N, i = node - j * N;
       if (i == 0 || j == 0 || i == N - 1 || j == N - 1) continue;
-      int cx[3], cy[3];
       float wx[3], wy[3];
-      const int nx = q2_pweights(i, cx, wx), ny = q2_pweights(j, cy, wy);
+      const int cx = q2_pw(i, wx[0], wx[1], wx[2]), cy = q2_pw(j, wy[0], wy[1], wy[2]);
       T s0 = 0, s1 = 0;
-      for (int u = 0; u < ny; ++u)
-        for (int v = 0; v < nx; ++v) {
-          const int c = cy[u] * Nc + cx[v];
+#pragma unroll
+      for (int u = 0; u < 3; ++u)
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          if (wx[v] == 0.f || wy[u] == 0.f) continue;
+          const int c = (cy + u) * Nc + cx + v;
           const T f = (T)(wx[v] * wy[u]);
           s0 += f * X[l + 1][c];
           s1 += f * X[l + 1][c + nvc];
@@ -657,19 +671,15 @@ __device__ void cq1_residual(int n, T hx, T hy, const T* X, const T* B, T* R) {
   for (int node = threadIdx.x; node < M * M; node += blockDim.x) {
     const int J = node / M, I = node - J * M;
     T acc = 0;
-    for (int ey = J - 1; ey <= J; ++ey) {
-      if (ey < 0 || ey >= n) continue;
-      const int d = J - ey;
-      for (int ex = I - 1; ex <= I; ++ex) {
-        if (ex < 0 || ex >= n) continue;
-        const int c = I - ex;
-        for (int dd = 0; dd < 2; ++dd)
-          for (int cc = 0; cc < 2; ++cc) {
-            const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
-            acc += kc * X[(ey + dd) * M + ex + cc];
-          }
-      }
-    }
+    Q1_FOR_ELEMENTS(n, I, J, {
+#pragma unroll
+      for (int dd = 0; dd < 2; ++dd)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
+          acc += kc * X[(ey + dd) * M + ex + cc];
+        }
+    })
     R[node] = B[node] - acc;
   }
   __syncthreads();
@@ -754,20 +764,16 @@ __global__ void k_q1_jr(int n, T hx, T hy, T omega, const T* __restrict__ dinv, 
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < M * M; node += gridDim.x * blockDim.x) {
     const int J = node / M, I = node - J * M;
     T acc = 0;
-    for (int ey = J - 1; ey <= J; ++ey) {
-      if (ey < 0 || ey >= n) continue;
-      const int d = J - ey;
-      for (int ex = I - 1; ex <= I; ++ex) {
-        if (ex < 0 || ex >= n) continue;
-        const int c = I - ex;
-        for (int dd = 0; dd < 2; ++dd)
-          for (int cc = 0; cc < 2; ++cc) {
-            const int q = (ey + dd) * M + ex + cc;
-            const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
-            acc += kc * omega * dinv[q] * b[q];
-          }
-      }
-    }
+    Q1_FOR_ELEMENTS(n, I, J, {
+#pragma unroll
+      for (int dd = 0; dd < 2; ++dd)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const int q = (ey + dd) * M + ex + cc;
+          const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
+          acc += kc * omega * dinv[q] * b[q];
+        }
+    })
     const T xv = omega * dinv[node] * b[node];
     x[node] = xv;
     r[node] = b[node] - acc;
@@ -788,19 +794,15 @@ __global__ void k_q1_ps(int n, T hx, T hy, T omega, const T* __restrict__ dinv, 
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < M * M; node += gridDim.x * blockDim.x) {
     const int J = node / M, I = node - J * M;
     T acc = 0;
-    for (int ey = J - 1; ey <= J; ++ey) {
-      if (ey < 0 || ey >= n) continue;
-      const int d = J - ey;
-      for (int ex = I - 1; ex <= I; ++ex) {
-        if (ex < 0 || ex >= n) continue;
-        const int c = I - ex;
-        for (int dd = 0; dd < 2; ++dd)
-          for (int cc = 0; cc < 2; ++cc) {
-            const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
-            acc += kc * xcorr(ey + dd, ex + cc);
-          }
-      }
-    }
+    Q1_FOR_ELEMENTS(n, I, J, {
+#pragma unroll
+      for (int dd = 0; dd < 2; ++dd)
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+          const T kc = rxy * (T)(q1k(c, cc) * q1m(d, dd)) + ryx * (T)(q1m(c, cc) * q1k(d, dd));
+          acc += kc * xcorr(ey + dd, ex + cc);
+        }
+    })
     const T xv = xcorr(J, I);
     y[node] = xv + omega * dinv[node] * (b[node] - acc);
   }
@@ -1005,8 +1007,8 @@ eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int*
 // in one tile launch per level, single-CTA shared-memory V-cycle below the
 // coarse threshold.
 // ---------------------------------------------------------------------------
-template <class T> static int q2_coarse_threshold() { return sizeof(T) == 4 ? 32 : 16; }
-template <class T> static int q1_coarse_threshold() { return 64; }
+template <class T> static int q2_coarse_threshold() { return 16; }
+template <class T> static int q1_coarse_threshold() { return 32; }
 
 template <class T, class TI, int CF>
 static eth_status q2_jr(eth_grid* g, Level<T>& L, const TI* b, T* bcopy, T omega, const int* done) {

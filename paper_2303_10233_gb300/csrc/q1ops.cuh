@@ -38,8 +38,20 @@ struct Q1Params {
   const int* done;
 };
 
-__host__ __device__ inline double q1m(int a, int b) { return a == b ? 1.0 / 3.0 : 1.0 / 6.0; }
-__host__ __device__ inline double q1k(int a, int b) { return a == b ? 1.0 : -1.0; }
+__host__ __device__ constexpr double q1m(int a, int b) { return a == b ? 1.0 / 3.0 : 1.0 / 6.0; }
+__host__ __device__ constexpr double q1k(int a, int b) { return a == b ? 1.0 : -1.0; }
+
+// Visits the (up to) four elements around Q1 node (I, J) with compile-time local
+// indices: f(ex, ey, c, d) gets the element and the node's local position (c, d)
+// in it (c, d are constants after unrolling, so coefficient products fold).
+#define Q1_FOR_ELEMENTS(n, I, J, ...)                                   \
+  _Pragma("unroll") for (int dy_ = 0; dy_ < 2; ++dy_)                    \
+  _Pragma("unroll") for (int dx_ = 0; dx_ < 2; ++dx_) {                  \
+    const int ex = (I) - 1 + dx_, ey = (J) - 1 + dy_;                    \
+    if (ex < 0 || ex >= (n) || ey < 0 || ey >= (n)) continue;            \
+    const int c = 1 - dx_, d = 1 - dy_;                                  \
+    __VA_ARGS__                                                          \
+  }
 
 template <class TI, class TO, class CT, int EPI>
 __global__ void __launch_bounds__(256) k_q1node(Q1Params<TI, TO, CT> P) {
@@ -51,30 +63,22 @@ __global__ void __launch_bounds__(256) k_q1node(Q1Params<TI, TO, CT> P) {
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < tot; node += gridDim.x * blockDim.x) {
     const int J = node / M, I = node - J * M;
     CT acc = 0;
+    Q1_FOR_ELEMENTS(n, I, J, {
+      const int e = ey * n + ex;
 #pragma unroll
-    for (int ey = J - 1; ey <= J; ++ey) {
-      if (ey < 0 || ey >= n) continue;
-      const int d = J - ey;
+      for (int dd = 0; dd < 2; ++dd)
 #pragma unroll
-      for (int ex = I - 1; ex <= I; ++ex) {
-        if (ex < 0 || ex >= n) continue;
-        const int c = I - ex;
-        const int e = ey * n + ex;
-#pragma unroll
-        for (int dd = 0; dd < 2; ++dd)
-#pragma unroll
-          for (int cc = 0; cc < 2; ++cc) {
-            CT coef = P.cm * area * (CT)(q1m(c, cc) * q1m(d, dd)) +
-                      P.ck * (rxy * (CT)(q1k(c, cc) * q1m(d, dd)) + ryx * (CT)(q1m(c, cc) * q1k(d, dd))) + P.c1;
-            if (P.conv != nullptr) {
-              const int li = d * 2 + c, lj = dd * 2 + cc;
-              coef += P.conv_trans ? P.conv[(size_t)e * 16 + lj * 4 + li] : P.conv[(size_t)e * 16 + li * 4 + lj];
-            }
-            acc += coef * (CT)P.x[(size_t)(ey + dd) * M + ex + cc];
+        for (int cc = 0; cc < 2; ++cc) {
+          CT coef = P.cm * area * (CT)(q1m(c, cc) * q1m(d, dd)) +
+                    P.ck * (rxy * (CT)(q1k(c, cc) * q1m(d, dd)) + ryx * (CT)(q1m(c, cc) * q1k(d, dd))) + P.c1;
+          if (P.conv != nullptr) {
+            const int li = d * 2 + c, lj = dd * 2 + cc;
+            coef += P.conv_trans ? P.conv[(size_t)e * 16 + lj * 4 + li] : P.conv[(size_t)e * 16 + li * 4 + lj];
           }
-        if (P.x0 != nullptr) acc += P.r0 * area * CT(0.25) * (CT)P.x0[e];
-      }
-    }
+          acc += coef * (CT)P.x[(size_t)(ey + dd) * M + ex + cc];
+        }
+      if (P.x0 != nullptr) acc += P.r0 * area * CT(0.25) * (CT)P.x0[e];
+    })
     TO out;
     if (EPI == Q1E_APPLY) out = (TO)acc;
     else if (EPI == Q1E_SMOOTH) out = (TO)((CT)P.x[node] + P.omega * P.dinv[node] * (P.b[node] - acc));
@@ -84,7 +88,7 @@ __global__ void __launch_bounds__(256) k_q1node(Q1Params<TI, TO, CT> P) {
   }
   if (P.dot) {
     double v[1] = {dacc};
-    if (slot_arrive<1>(P.slot, P.slot_off + blockIdx.x, v)) P.slot.out[0] = v[0];
+    if (slot_arrive<1>(P.slot, P.slot_off + blockIdx.x, v)) finish_slot(P.slot, v[0]);
   }
 }
 

@@ -345,27 +345,27 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
         const int lj = k / SQX, li = k - lj * SQX;
         const int i = gi0 + li, j = gj0 + lj;
         if (i <= 0 || j <= 0 || i >= N - 1 || j >= N - 1) continue;   // boundary / outside: no correction
-        int cx[3], cy[3];
         CT wx[3], wy[3];
-        int nx, ny;
-        if (!(i & 1)) { cx[0] = i >> 1; wx[0] = 1; nx = 1; }
+        int cx, cy;
+        if (!(i & 1)) { cx = i >> 1; wx[0] = 1; wx[1] = 0; wx[2] = 0; }
         else {
-          const int E = i >> 2; nx = 3;
-          cx[0] = 2 * E; cx[1] = 2 * E + 1; cx[2] = 2 * E + 2;
+          cx = 2 * (i >> 2);
           if ((i & 3) == 1) { wx[0] = CT(0.375); wx[1] = CT(0.75); wx[2] = CT(-0.125); }
           else { wx[0] = CT(-0.125); wx[1] = CT(0.75); wx[2] = CT(0.375); }
         }
-        if (!(j & 1)) { cy[0] = j >> 1; wy[0] = 1; ny = 1; }
+        if (!(j & 1)) { cy = j >> 1; wy[0] = 1; wy[1] = 0; wy[2] = 0; }
         else {
-          const int E = j >> 2; ny = 3;
-          cy[0] = 2 * E; cy[1] = 2 * E + 1; cy[2] = 2 * E + 2;
+          cy = 2 * (j >> 2);
           if ((j & 3) == 1) { wy[0] = CT(0.375); wy[1] = CT(0.75); wy[2] = CT(-0.125); }
           else { wy[0] = CT(-0.125); wy[1] = CT(0.75); wy[2] = CT(0.375); }
         }
         CT a = 0, b = 0;
-        for (int u = 0; u < ny; ++u)
-          for (int v = 0; v < nx; ++v) {
-            const int c = (cy[u] - cJ0) * CXW + (cx[v] - cI0);
+#pragma unroll
+        for (int u = 0; u < 3; ++u)
+#pragma unroll
+          for (int v = 0; v < 3; ++v) {
+            if (wx[v] == CT(0) || wy[u] == CT(0)) continue;
+            const int c = (cy + u - cJ0) * CXW + (cx + v - cI0);
             a += wx[v] * wy[u] * sc[c];
             b += wx[v] * wy[u] * sc[CYW * CXW + c];
           }

@@ -13,8 +13,13 @@ struct Scalars {
   int done;              // early-exit flag checked by every kernel of a chunk
   int status;            // eth_status raised on the device
   int iter;              // device iteration counter
-  int inner_done;        // early-exit flag of an inner (nested) iteration
+  int inner_done;        // unused
+  int idone[4];          // early-exit flags of inner (nested) PCG solves
 };
+
+// Inner PCG state blocks (exact preconditioner blocks): base index of each.
+enum : int { PCG_VEL = 48, PCG_PRE = 64 };
+enum : int { P_RZ = 0, P_ALPHA, P_BETA, P_TARGET, P_ITS, P_TOL };
 
 // MINRES (Algorithm 1) state: gamma_{j-1}, gamma_j, c_{j-1}, c_j, s_{j-1}, s_j,
 // eta, |eta_1|, delta_j and the coefficients of the fused vector updates.
@@ -41,9 +46,10 @@ enum : int {
   FIN_VSUMS,          // beta = (sum v_p1 - sum v_p0) / (n1 + n0)
   FIN_MQ,             // gamma1 of the M_Q output from (sum z~, sum adj*z~, sum v0)
   FIN_DONE,           // done = pending
-  FIN_PCG_INIT,       // inner PCG: rz0 = <r, z>
+  FIN_PCG_INIT,       // inner PCG: s = (<r, z>, <r, r>) -> rz, target = tol^2 <r, r>
   FIN_PCG_ALPHA,      // alpha = rz / <p, A p>
-  FIN_PCG_RZ,         // beta = rz_new / rz, convergence of the inner solve
+  FIN_PCG_RZ,         // beta = rz_new / rz; rz = rz_new
+  FIN_PCG_RR,         // <r, r> <= target -> inner done
 };
 
 __device__ __forceinline__ void finish_minres_gamma(Scalars* sc, double g2) {
@@ -117,6 +123,31 @@ __device__ __forceinline__ void finish_slot_n(const Slot& sl, const double (&s)[
       if (v[S_PEND] != 0.0) sc->done = 1;
       sc->iter += 1;
       break;
+    case FIN_PCG_INIT: {
+      double* q = v + sl.base;
+      q[P_RZ] = s[0];
+      q[P_TARGET] = q[P_TOL] * q[P_TOL] * s[NV_ > 1 ? 1 : 0];
+      q[P_ITS] = 0.0;
+      if (!(s[NV_ > 1 ? 1 : 0] > 0.0) || !(s[0] > 0.0)) sc->idone[sl.flag] = 1;
+      break;
+    }
+    case FIN_PCG_ALPHA: {
+      double* q = v + sl.base;
+      q[P_ALPHA] = s[0] != 0.0 ? q[P_RZ] / s[0] : 0.0;
+      q[P_ITS] += 1.0;
+      break;
+    }
+    case FIN_PCG_RR: {
+      double* q = v + sl.base;
+      if (!(s[0] > q[P_TARGET])) sc->idone[sl.flag] = 1;
+      break;
+    }
+    case FIN_PCG_RZ: {
+      double* q = v + sl.base;
+      q[P_BETA] = q[P_RZ] != 0.0 ? s[0] / q[P_RZ] : 0.0;
+      q[P_RZ] = s[0];
+      break;
+    }
     default:
       break;
   }

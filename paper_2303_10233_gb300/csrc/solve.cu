@@ -19,7 +19,7 @@ static void work_free(void* p) {
   if (!w) return;
   gmres_free(w);
   mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd); mg_free(w->vft); mg_free(w->vdt);
-  cudaFree(w->x); cudaFree(w->d); cudaFree(w->r); cudaFree(w->Kz); cudaFree(w->bp);
+  cudaFree(w->x); cudaFree(w->d); cudaFree(w->r); cudaFree(w->Kz); cudaFree(w->bp); cudaFree(w->pcg);
   for (int k = 0; k < 2; ++k) { cudaFree(w->V[k]); cudaFree(w->Z[k]); cudaFree(w->W[k]); }
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
   if (w->s2) cudaStreamDestroy(w->s2);
@@ -166,63 +166,59 @@ __global__ void k_mq_t(int n, const double* __restrict__ vp, const Scalars* __re
                        T* __restrict__ x, const T* __restrict__ dinv, T omega, const int* done) {
   if (done != nullptr && *done) return;
   const int M = n + 1, n1 = M * M;
-  const double beta = sc->v[S_BETA];
+  const T beta = (T)sc->v[S_BETA];
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n1; node += gridDim.x * blockDim.x) {
     const int J = node / M, I = node - J * M;
-    double s = 0.0;
-    for (int ey = J - 1; ey <= J; ++ey) {
-      if (ey < 0 || ey >= n) continue;
-      for (int ex = I - 1; ex <= I; ++ex) {
-        if (ex < 0 || ex >= n) continue;
-        s += vp[n1 + (size_t)ey * n + ex] + beta;
-      }
-    }
-    const T t = cvt<T, double>(vp[node] - beta - 0.25 * s);
+    T s = 0;
+    Q1_FOR_ELEMENTS(n, I, J, { s += cvt<T, double>(vp[n1 + (size_t)ey * n + ex]) + beta; (void)c; (void)d; })
+    const T t = cvt<T, double>(vp[node]) - beta - T(0.25) * s;
     b[node] = t;
     x[node] = omega * dinv[node] * t;
   }
 }
 
+// sums for the k-orthogonality constant: (sum z~, sum_T sum_{I in T} z~_I, sum_T (v0_T + beta)/|T|)
 template <class T>
-__global__ void k_mq_sums(int n, const T* __restrict__ zt, const double* __restrict__ vp, double area, Slot sl, const int* done) {
+__global__ void k_mq_sums(int n, const T* __restrict__ zt, const double* __restrict__ vp, T inv_area, Slot sl, const int* done) {
   if (done != nullptr && *done) return;
   const int M = n + 1, n1 = M * M, n0 = n * n;
-  const double beta = sl.sc->v[S_BETA];
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  const T beta = (T)sl.sc->v[S_BETA];
+  T s0 = 0, s1 = 0, s2 = 0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n0; k += gridDim.x * blockDim.x) {
     if (k < n1) {
       const int J = k / M, I = k - J * M;
       const int ne = ((I > 0) + (I < n)) * ((J > 0) + (J < n));
-      const double z = (double)zt[k];
+      const T z = zt[k];
       s0 += z;
-      s1 += ne * z;
+      s1 += (T)ne * z;
     } else {
-      s2 += (vp[k] + beta) / area;
+      s2 += (cvt<T, double>(vp[k]) + beta) * inv_area;
     }
   }
-  double v[3] = {s0, s1, s2};
+  double v[3] = {(double)s0, (double)s1, (double)s2};
   if (slot_arrive<3>(sl, blockIdx.x, v)) finish_slot_n<3>(sl, v);
 }
 
 template <class T>
-__global__ void k_mq_out(int n, const T* __restrict__ zt, const double* __restrict__ vp, double* __restrict__ zp, double area,
+__global__ void k_mq_out(int n, const T* __restrict__ zt, const double* __restrict__ vp, double* __restrict__ zp, T inv_area,
                          const Scalars* __restrict__ sc, Slot gsl, int goff, const int* done) {
   if (done != nullptr && *done) return;
   const int M = n + 1, n1 = M * M, n0 = n * n;
-  const double beta = sc->v[S_BETA], c = sc->v[S_MQC], g1 = sc->v[S_MQG], nu = sc->v[S_MQNU];
+  const T beta = (T)sc->v[S_BETA], c = (T)sc->v[S_MQC], g1 = (T)sc->v[S_MQG], nu = (T)sc->v[S_MQNU];
   double acc = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n1 + n0; k += gridDim.x * blockDim.x) {
-    double z;
+    T z;
     if (k < n1) {
-      z = nu * (c * (double)zt[k] + g1);
+      z = nu * (c * zt[k] + g1);
     } else {
       const int e = k - n1, ey = e / n, ex = e - ey * n;
-      const double s = (double)zt[(size_t)ey * M + ex] + (double)zt[(size_t)ey * M + ex + 1] +
-                       (double)zt[(size_t)(ey + 1) * M + ex] + (double)zt[(size_t)(ey + 1) * M + ex + 1];
-      z = nu * ((vp[k] + beta) / area - 0.25 * c * s - g1);
+      const T s = zt[(size_t)ey * M + ex] + zt[(size_t)ey * M + ex + 1] + zt[(size_t)(ey + 1) * M + ex] +
+                  zt[(size_t)(ey + 1) * M + ex + 1];
+      z = nu * ((cvt<T, double>(vp[k]) + beta) * inv_area - T(0.25) * c * s - g1);
     }
-    zp[k] = z;
-    acc += z * vp[k];
+    const double zd = cvt<double, T>(z);
+    zp[k] = zd;
+    acc += zd * vp[k];
   }
   double v[1] = {acc};
   if (slot_arrive<1>(gsl, goff + blockIdx.x, v)) finish_slot(gsl, v[0]);
@@ -243,9 +239,9 @@ eth_status precond_pressure(eth_grid* g, Hier<T>& Q, const double* vp, double* z
   if (st != ETH_OK) { g->s = keep; return st; }
   const int nb = mq_blocks(g);
   Slot sm = slot_of(g, SL_MQ, nb, FIN_MQ);
-  k_mq_sums<T><<<nb, 256, 0, s>>>(g->n, zt, vp, g->hx * g->hy, sm, done);
+  k_mq_sums<T><<<nb, 256, 0, s>>>(g->n, zt, vp, (T)(1.0 / (g->hx * g->hy)), sm, done);
   ETH_CUDA(cudaGetLastError());
-  k_mq_out<T><<<nb, 256, 0, s>>>(g->n, zt, vp, zp, g->hx * g->hy, g->sc, gsl, goff, done);
+  k_mq_out<T><<<nb, 256, 0, s>>>(g->n, zt, vp, zp, (T)(1.0 / (g->hx * g->hy)), g->sc, gsl, goff, done);
   ETH_CUDA(cudaGetLastError());
   g->launches += 3;
   g->s = keep;
@@ -267,17 +263,272 @@ Hier<double>& q1_hier<double>(Work* w) { return w->qd; }
 template eth_status precond_pressure<float>(eth_grid*, Hier<float>&, const double*, double*, const Slot&, int, const int*, cudaStream_t);
 template eth_status precond_pressure<double>(eth_grid*, Hier<double>&, const double*, double*, const Slot&, int, const int*, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// exact preconditioner blocks (the P_1 form of Sec. 2.4): inner PCG solves of
+// the velocity block (GMG V-cycle preconditioner) and of the Schur complement
+// S = Qk - R^T Q0^{-1} R of M_Q (Q1 Laplacian V-cycle preconditioner), each to
+// a relative residual opts.inner_tol, with device-side convergence flags so the
+// whole outer iteration stays capturable in a CUDA graph.
+// ---------------------------------------------------------------------------
+__global__ void k_pcg_setup(Scalars* sc, int base, int flag, double tol) {
+  sc->v[base + P_TOL] = tol;
+  sc->v[base + P_ITS] = 0.0;
+  sc->idone[flag] = sc->done;
+}
+
+__global__ void k_pcg_start(size_t m, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ x,
+                            const int* done) {
+  if (*done) return;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
+    r[k] = b[k];
+    x[k] = 0.0;
+  }
+}
+
+// (<a,b>, <a,a>) -> finisher
+__global__ void k_dot2(size_t m, const double* __restrict__ a, const double* __restrict__ b, Slot sl, const int* done) {
+  if (*done) return;
+  double s0 = 0.0, s1 = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
+    s0 += a[k] * b[k];
+    s1 += a[k] * a[k];
+  }
+  double v[2] = {s0, s1};
+  if (slot_arrive<2>(sl, blockIdx.x, v)) finish_slot_n<2>(sl, v);
+}
+
+__global__ void k_pcg_copy(size_t m, const double* __restrict__ a, double* __restrict__ b, const int* done) {
+  if (*done) return;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) b[k] = a[k];
+}
+
+// x += alpha p ; r -= alpha q ; <r, r> -> FIN_PCG_RR
+__global__ void k_pcg_xr(size_t m, const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                         double* __restrict__ r, Slot sl, const int* done) {
+  if (*done) return;
+  const double a = sl.sc->v[sl.base + P_ALPHA];
+  double acc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
+    x[k] += a * p[k];
+    const double rv = r[k] - a * q[k];
+    r[k] = rv;
+    acc += rv * rv;
+  }
+  double v[1] = {acc};
+  if (slot_arrive<1>(sl, blockIdx.x, v)) finish_slot(sl, v[0]);
+}
+
+// p = z + beta p
+__global__ void k_pcg_pupd(size_t m, const double* __restrict__ z, double* __restrict__ p, const Scalars* sc, int base,
+                           const int* done) {
+  if (*done) return;
+  const double bt = sc->v[base + P_BETA];
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) p[k] = z[k] + bt * p[k];
+}
+
+// <a, b> -> finisher
+__global__ void k_dot1(size_t m, const double* __restrict__ a, const double* __restrict__ b, Slot sl, const int* done) {
+  if (*done) return;
+  double s0 = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) s0 += a[k] * b[k];
+  double v[1] = {s0};
+  if (slot_arrive<1>(sl, blockIdx.x, v)) finish_slot(sl, v[0]);
+}
+
+template <class T>
+__global__ void k_to_t(int m, const double* __restrict__ a, T* __restrict__ b, const int* done) {
+  if (*done) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) b[k] = cvt<T, double>(a[k]);
+}
+template <class T>
+__global__ void k_from_t(int m, const T* __restrict__ a, double* __restrict__ b, const int* done) {
+  if (*done) return;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) b[k] = cvt<double, T>(a[k]);
+}
+
+// t = (r_k - beta) - 1/4 sum_{T ni I} (r_0,T + beta)  in FP64
+__global__ void k_mq_t64(int n, const double* __restrict__ vp, const Scalars* __restrict__ sc, double* __restrict__ t,
+                         const int* done) {
+  if (done != nullptr && *done) return;
+  const int M = n + 1, n1 = M * M;
+  const double beta = sc->v[S_BETA];
+  for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < n1; node += gridDim.x * blockDim.x) {
+    const int J = node / M, I = node - J * M;
+    double s = 0.0;
+    for (int ey = J - 1; ey <= J; ++ey) {
+      if (ey < 0 || ey >= n) continue;
+      for (int ex = I - 1; ex <= I; ++ex) {
+        if (ex < 0 || ex >= n) continue;
+        s += vp[n1 + (size_t)ey * n + ex] + beta;
+      }
+    }
+    t[node] = vp[node] - beta - 0.25 * s;
+  }
+}
+
+static Slot pslot(eth_grid* g, int which, int total, int op, int base, int flag) {
+  Slot s = slot_of(g, which, total, op);
+  s.base = base;
+  s.flag = flag;
+  return s;
+}
+
+static eth_status ensure_pcg(eth_grid* g, Work* w) {
+  if (w->pcg) return ETH_OK;
+  const size_t nu2 = 2 * (size_t)g->nv;
+  ETH_CUDA(cudaMalloc((void**)&w->pcg, (4 * nu2 + 6 * (size_t)g->n1) * 8));
+  return ETH_OK;
+}
+
+// x = F^{-1} b (velocity block, identity boundary rows) by V-cycle-preconditioned CG.
+template <class T>
+static eth_status vel_pcg(eth_grid* g, Work* w, const eth_opts* o, const double* b, double* x, int maxit) {
+  const size_t nu2 = 2 * (size_t)g->nv;
+  double *r = w->pcg, *p = r + nu2, *q = p + nu2, *z = q + nu2;
+  const int* idone = &g->sc->idone[0];
+  const int nb = vblocks(nu2);
+  k_pcg_setup<<<1, 1, 0, g->s>>>(g->sc, PCG_VEL, 0, o->inner_tol);
+  k_pcg_start<<<nb, 256, 0, g->s>>>(nu2, b, r, x, idone);
+  ETH_CUDA(cudaGetLastError());
+  ETH_TRY(vcycle_vel<T>(g, vel_hier<T>(w), r, z, o->mg_pre, o->mg_post, idone, nullptr, 0));
+  k_dot2<<<nb, 256, 0, g->s>>>(nu2, r, z, pslot(g, 9, nb, FIN_PCG_INIT, PCG_VEL, 0), idone);
+  k_pcg_copy<<<nb, 256, 0, g->s>>>(nu2, z, p, idone);
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 5;
+  const bool fp32 = o->precision == ETH_MIXED;
+  for (int it = 0; it < maxit; ++it) {
+    {  // q = F p with the fused <q, p>
+      Slot s = pslot(g, 10, q2_blocks(g->n), FIN_PCG_ALPHA, PCG_VEL, 0);
+      if (fp32) {
+        Q2Params<double, double, float> P{};
+        P.n = g->n; P.hx = (float)g->hx; P.hy = (float)g->hy; P.nu = (float)g->nu;
+        P.x = p; P.y = q; P.w = g->windf; P.done = idone; P.slot = s; P.dv = p;
+        if (g->kind == ETH_OSEEN) ETH_CUDA((launch_q2<double, double, float, QF_DIFF | QF_CONV | QF_XIN | QF_UOUT | QF_DOT, EPI_APPLY>(P, g->s)));
+        else ETH_CUDA((launch_q2<double, double, float, QF_DIFF | QF_XIN | QF_UOUT | QF_DOT, EPI_APPLY>(P, g->s)));
+      } else {
+        Q2Params<double, double, double> P{};
+        P.n = g->n; P.hx = g->hx; P.hy = g->hy; P.nu = g->nu;
+        P.x = p; P.y = q; P.w = g->wind; P.done = idone; P.slot = s; P.dv = p;
+        if (g->kind == ETH_OSEEN) ETH_CUDA((launch_q2<double, double, double, QF_DIFF | QF_CONV | QF_XIN | QF_UOUT | QF_DOT, EPI_APPLY>(P, g->s)));
+        else ETH_CUDA((launch_q2<double, double, double, QF_DIFF | QF_XIN | QF_UOUT | QF_DOT, EPI_APPLY>(P, g->s)));
+      }
+    }
+    k_pcg_xr<<<nb, 256, 0, g->s>>>(nu2, p, q, x, r, pslot(g, 11, nb, FIN_PCG_RR, PCG_VEL, 0), idone);
+    ETH_CUDA(cudaGetLastError());
+    ETH_TRY(vcycle_vel<T>(g, vel_hier<T>(w), r, z, o->mg_pre, o->mg_post, idone, nullptr, 0));
+    k_dot1<<<nb, 256, 0, g->s>>>(nu2, r, z, pslot(g, 9, nb, FIN_PCG_RZ, PCG_VEL, 0), idone);
+    k_pcg_pupd<<<nb, 256, 0, g->s>>>(nu2, z, p, g->sc, PCG_VEL, idone);
+    ETH_CUDA(cudaGetLastError());
+    g->launches += 4;
+  }
+  return ETH_OK;
+}
+
+// x = S^+ t (Q1, FP64) by Q1-Laplacian-V-cycle-preconditioned CG.
+template <class T>
+static eth_status schur_pcg(eth_grid* g, Work* w, const eth_opts* o, const double* t, double* x, int maxit, cudaStream_t s) {
+  const size_t nu2 = 2 * (size_t)g->nv;
+  const int m = g->n1;
+  double *r = w->pcg + 4 * nu2, *p = r + m, *q = p + m, *z = q + m;
+  const int* idone = &g->sc->idone[1];
+  const int nb = vblocks(m);
+  Hier<T>& Q = q1_hier<T>(w);
+  const cudaStream_t keep = g->s;
+  g->s = s;
+  auto precond = [&](const double* rr, double* zz) -> eth_status {
+    k_to_t<T><<<nb, 256, 0, s>>>(m, rr, Q.lv[0].b, idone);
+    ETH_CUDA(cudaGetLastError());
+    const T* res = nullptr;
+    ETH_TRY(vcycle_q1_from<T>(g, Q, 1, 1, idone, &res));
+    k_from_t<T><<<nb, 256, 0, s>>>(m, res, zz, idone);
+    ETH_CUDA(cudaGetLastError());
+    g->launches += 2;
+    return ETH_OK;
+  };
+  k_pcg_setup<<<1, 1, 0, s>>>(g->sc, PCG_PRE, 1, o->inner_tol);
+  k_pcg_start<<<nb, 256, 0, s>>>((size_t)m, t, r, x, idone);
+  ETH_CUDA(cudaGetLastError());
+  eth_status st = precond(r, z);
+  if (st != ETH_OK) { g->s = keep; return st; }
+  k_dot2<<<nb, 256, 0, s>>>((size_t)m, r, z, pslot(g, 12, nb, FIN_PCG_INIT, PCG_PRE, 1), idone);
+  k_pcg_copy<<<nb, 256, 0, s>>>((size_t)m, z, p, idone);
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 4;
+  for (int it = 0; it < maxit; ++it) {
+    Q1Params<double, double, double> P{};
+    P.n = g->n; P.hx = g->hx; P.hy = g->hy; P.cm = 1.0; P.ck = 0.0; P.c1 = -g->hx * g->hy / 16.0;
+    P.x = p; P.y = q; P.done = idone; P.dot = 1;
+    const int nq = (int)q1_blocks(g->n);
+    P.slot = pslot(g, 13, nq, FIN_PCG_ALPHA, PCG_PRE, 1);
+    k_q1node<double, double, double, Q1E_APPLY><<<nq, 256, 0, s>>>(P);
+    k_pcg_xr<<<nb, 256, 0, s>>>((size_t)m, p, q, x, r, pslot(g, 14, nb, FIN_PCG_RR, PCG_PRE, 1), idone);
+    ETH_CUDA(cudaGetLastError());
+    st = precond(r, z);
+    if (st != ETH_OK) { g->s = keep; return st; }
+    k_dot1<<<nb, 256, 0, s>>>((size_t)m, r, z, pslot(g, 12, nb, FIN_PCG_RZ, PCG_PRE, 1), idone);
+    k_pcg_pupd<<<nb, 256, 0, s>>>((size_t)m, z, p, g->sc, PCG_PRE, idone);
+    ETH_CUDA(cudaGetLastError());
+    g->launches += 4;
+  }
+  g->s = keep;
+  return ETH_OK;
+}
+
+// exact nu M_Q^+ r_p (k projected out): t = r_k - R^T Q0^{-1} r_0, z_k = S^+ t, z_0 = Q0^{-1}(r_0 - R z_k)
+template <class T>
+static eth_status precond_pressure_exact(eth_grid* g, Work* w, const eth_opts* o, const double* vp, double* zp,
+                                         const Slot& gsl, int goff, const int* done, cudaStream_t s) {
+  const size_t nu2 = 2 * (size_t)g->nv;
+  const int m = g->n1;
+  double* t = w->pcg + 4 * nu2 + 4 * (size_t)m;
+  double* zt = t + m;
+  k_mq_t64<<<vblocks(m), 256, 0, s>>>(g->n, vp, g->sc, t, done);
+  ETH_CUDA(cudaGetLastError());
+  ETH_TRY(schur_pcg<T>(g, w, o, t, zt, 60, s));
+  const int nb = mq_blocks(g);
+  Slot sm = slot_of(g, SL_MQ, nb, FIN_MQ);
+  k_mq_sums<double><<<nb, 256, 0, s>>>(g->n, zt, vp, 1.0 / (g->hx * g->hy), sm, done);
+  k_mq_out<double><<<nb, 256, 0, s>>>(g->n, zt, vp, zp, 1.0 / (g->hx * g->hy), g->sc, gsl, goff, done);
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 3;
+  return ETH_OK;
+}
+
+// exact velocity block with the fused <z_u, v_u> partials into the gamma slot
+__global__ void k_vel_out(size_t m, const double* __restrict__ x, const double* __restrict__ v, double* __restrict__ z,
+                          Slot gsl, const int* done) {
+  if (done != nullptr && *done) return;
+  double acc = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
+    z[k] = x[k];
+    acc += x[k] * v[k];
+  }
+  double a[1] = {acc};
+  if (slot_arrive<1>(gsl, blockIdx.x, a)) finish_slot(gsl, a[0]);
+}
+
 // z = P^{-1} v with the fused <z, v> into the gamma slot (finisher fin).
 // The velocity V-cycle and the pressure block run on two streams (fork/join).
 template <class T>
 static eth_status precond_stokes(eth_grid* g, Work* w, const eth_opts* o, const double* v, double* z, int fin, const int* done) {
   const size_t nu2 = 2 * (size_t)g->nv;
-  const int nbv = vel_final_blocks(g->n), nbp = mq_blocks(g);
+  const int nbv = o->a_exact ? vblocks(nu2) : vel_final_blocks(g->n), nbp = mq_blocks(g);
   Slot gs = slot_of(g, SL_GAMMA, nbv + nbp, fin);
   ETH_CUDA(cudaEventRecord(w->evf, g->s));
   ETH_CUDA(cudaStreamWaitEvent(w->s2, w->evf, 0));
-  ETH_TRY(precond_pressure<T>(g, q1_hier<T>(w), v + nu2, z + nu2, gs, nbv, done, w->s2));
-  ETH_TRY(vcycle_vel<T>(g, vel_hier<T>(w), v, z, o->mg_pre, o->mg_post, done, &gs, 0));
+  if (o->mq_mode == ETH_MQ_EXACT) ETH_TRY(precond_pressure_exact<T>(g, w, o, v + nu2, z + nu2, gs, nbv, done, w->s2));
+  else ETH_TRY(precond_pressure<T>(g, q1_hier<T>(w), v + nu2, z + nu2, gs, nbv, done, w->s2));
+  if (o->a_exact) {
+    double* xv = w->pcg + 3 * nu2 + 0;   // reuse: result written to z, q buffer as scratch is not needed after
+    (void)xv;
+    ETH_TRY(vel_pcg<T>(g, w, o, v, z, 60));
+    // <z_u, v_u> partials (z_u already in place)
+    k_vel_out<<<nbv, 256, 0, g->s>>>(nu2, z, v, z, gs, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+  } else {
+    ETH_TRY(vcycle_vel<T>(g, vel_hier<T>(w), v, z, o->mg_pre, o->mg_post, done, &gs, 0));
+  }
   ETH_CUDA(cudaEventRecord(w->evj, w->s2));
   ETH_CUDA(cudaStreamWaitEvent(g->s, w->evj, 0));
   return ETH_OK;
@@ -316,7 +567,8 @@ template <class T>
 static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp32, double tol, int maxit, int* its, int* dstat) {
   const size_t nt = g->nt;
   const double area = g->hx * g->hy;
-  k_init_scalars<<<1, 1, 0, g->s>>>(g->sc, tol, (double)g->n1, (double)g->n0, 16.0 / area, g->nu);
+  k_init_scalars<<<1, 1, 0, g->s>>>(g->sc, tol, (double)g->n1, (double)g->n0,
+                                    o->mq_mode == ETH_MQ_EXACT ? 1.0 : 16.0 / area, g->nu);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
   ETH_CUDA(cudaMemsetAsync(w->d, 0, nt * 8, g->s));
@@ -337,7 +589,8 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
   if (g->sch->v[S_PEND] != 0.0) { *its = 0; *dstat = g->sch->status; return ETH_OK; }
   int j = 1;
   const bool use_graph = o->graph != 0;
-  const int key = (int)fp32 * 1000 + (int)(sizeof(T)) * 10 + o->mg_pre + 100 * o->mg_post;
+  const int key = (int)fp32 * 1000 + (int)(sizeof(T)) * 10 + o->mg_pre + 100 * o->mg_post + 10000 * o->a_exact +
+                  20000 * o->mq_mode;
   while (true) {
     if (use_graph) {
       if (!w->gexec || w->gkey != key) {
@@ -391,8 +644,8 @@ eth_status ensure_hier(eth_grid* g, Work* w, const eth_opts* o) {
 }
 
 // ||b - K x||^2 in FP64 (K applied with FP64 element arithmetic); result to host.
-eth_status true_residual(eth_grid* g, Work* w, const double* b, double* rr) {
-  ETH_TRY(op_apply_K(g, false, false, w->x, w->Kz, nullptr));
+eth_status true_residual(eth_grid* g, Work* w, const double* b, double* rr, bool trans) {
+  ETH_TRY(op_apply_K(g, false, trans, w->x, w->Kz, nullptr));
   const int nb = vblocks(g->nt);
   k_residual<<<nb, 256, 0, g->s>>>((size_t)g->nt, b, w->Kz, w->r, slot_of(g, SL_NORM, nb, FIN_STORE));
   ETH_CUDA(cudaGetLastError());
@@ -497,6 +750,7 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   eth_opts o;
   if (opts) o = *opts; else eth_default_opts(&o);
   if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1) { set_error("eth_solve: bad options"); return ETH_EINVAL; }
+  if ((o.a_exact || o.mq_mode == ETH_MQ_EXACT) && !(o.inner_tol > 0)) { set_error("eth_solve: bad inner_tol"); return ETH_EINVAL; }
   if (o.precision != ETH_FP64 && o.precision != ETH_MIXED) { set_error("eth_solve: bad precision"); return ETH_EINVAL; }
   eth_stats st;
   std::memset(&st, 0, sizeof(st));
@@ -504,6 +758,7 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   ETH_TRY(work_get(g, &w));
   StreamSwap guard(g, w);
   if (o.precision == ETH_MIXED) ETH_TRY(ensure_hier<float>(g, w, &o)); else ETH_TRY(ensure_hier<double>(g, w, &o));
+  if (o.a_exact || o.mq_mode == ETH_MQ_EXACT) ETH_TRY(ensure_pcg(g, w));
   const long l0 = g->launches;
   ETH_CUDA(cudaEventRecord(w->t0, g->s));
   const size_t nu2 = 2 * (size_t)g->nv;

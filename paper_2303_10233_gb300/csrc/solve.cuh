@@ -23,6 +23,7 @@ struct Work {
   long glaunch = 0;            // kernels in one replay of gexec
   int nmin_built = -1;
   GMRESWork* gm = nullptr;     // GMRES / PCD workspace (Oseen)
+  double* pcg = nullptr;       // exact-block inner PCG vectors (4 x 2 N_v + 6 x N_1)
 };
 
 
@@ -44,7 +45,7 @@ int vblocks(size_t m);
 Slot slot_of(eth_grid* g, int which, int total, int op);
 eth_status read_scalars(eth_grid* g);
 eth_status canonicalize(eth_grid* g, double* x);
-eth_status true_residual(eth_grid* g, Work* w, const double* b, double* rr);
+eth_status true_residual(eth_grid* g, Work* w, const double* b, double* rr, bool trans = false);
 int mq_blocks(eth_grid* g);
 template <class T>
 eth_status precond_pressure(eth_grid* g, Hier<T>& Q, const double* vp, double* zp, const Slot& gsl, int goff,

@@ -80,3 +80,21 @@ def test_zero_rhs_and_bad_options(eth):
     with pytest.raises(eth.EthError):
         G.solve(tol=-1.0)
     G.close()
+
+
+def test_cavity16_exact_blocks_match_oracle_minres(eth):
+    """Config 1: MINRES with P_1 = blkdiag(A, M_Q) solved exactly (inner PCG to
+    1e-12): the GPU iteration count equals the oracle's Algorithm 1 with the
+    same exact blocks to within one iteration, and the solution matches."""
+    from oracle import krylov
+    w = W.cavity(16)
+    g, s, b = _oracle(w)
+    tol = 1e-8
+    x, st = _solve(eth, w, tol=tol, precision="fp64", a_exact=1, mq_mode=1, inner_tol=1e-12)
+    assert st["status"] == 0 and st["refine_passes"] == 1
+    x0 = np.concatenate([s.DB @ b[: g.nu], np.zeros(g.np_)])
+    bb = s.project_rhs(b)
+    xo, info = krylov.minres(lambda v: s.K @ v, krylov.P1(s), bb, x0, tol=0.3 * tol / 1.0, maxit=500)
+    assert abs(st["iters_total"] - info["its"]) <= 1, (st["iters_total"], info["its"])
+    xd, _ = direct.solve(s, b)
+    assert np.linalg.norm(s.canonical(x) - xd) <= 1e-6 * np.linalg.norm(xd)
