@@ -35,8 +35,12 @@ def _headers():
     return glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def build(verbose=False, extra=()):
+def build(verbose=False, extra=(), force=False):
     os.makedirs(OUT, exist_ok=True)
+    extra = list(extra) + os.environ.get("ETH_NVCC_EXTRA", "").split()
+    if force:
+        for f in glob.glob(os.path.join(OUT, "*.o")):
+            os.remove(f)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_t = max([os.path.getmtime(h) for h in _headers()] + [os.path.getmtime(__file__)])
     nvcc = _nvcc()

@@ -549,6 +549,46 @@ __device__ void cq2_residual(int n, T hx, T hy, T nu, T sd, const T* __restrict_
   }
 }
 
+// Node-parallel residual R = B - nu A X for the Stokes levels of the coarse
+// kernel: every interior node sums its (up to four) element rows from the
+// closed-form element matrix (tables KM, MK in shared memory), so all threads
+// work on every pass (no colour phases).
+template <class T>
+__device__ void cq2_residual_node(int n, T hx, T hy, T nu, const T* KM, const T* MK, const T* X, const T* B, T* R) {
+  const int N = 2 * n + 1, nv = N * N;
+  const T skm = nu * hy / hx, smk = nu * hx / hy;
+  for (int node = threadIdx.x; node < nv; node += blockDim.x) {
+    const int j = node / N, i = node - j * N;
+    if (i == 0 || j == 0 || i == N - 1 || j == N - 1) { R[node] = 0; R[node + nv] = 0; continue; }
+    int ex0, ex1, a0, a1, nx, ey0, ey1, b0, b1, ny;
+    if (i & 1) { ex0 = i >> 1; a0 = 1; ex1 = ex0; a1 = a0; nx = 1; } else { ex0 = (i >> 1) - 1; a0 = 2; ex1 = i >> 1; a1 = 0; nx = 2; }
+    if (j & 1) { ey0 = j >> 1; b0 = 1; ey1 = ey0; b1 = b0; ny = 1; } else { ey0 = (j >> 1) - 1; b0 = 2; ey1 = j >> 1; b1 = 0; ny = 2; }
+    T acc0 = 0, acc1 = 0;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (u >= ny) break;
+      const int ey = u ? ey1 : ey0, bb = u ? b1 : b0;
+#pragma unroll
+      for (int v = 0; v < 2; ++v) {
+        if (v >= nx) break;
+        const int ex = v ? ex1 : ex0, aa = v ? a1 : a0;
+        const int row = (bb * 3 + aa) * 9;
+        const int g0 = 2 * ey * N + 2 * ex;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+          const T cf = skm * KM[row + q] + smk * MK[row + q];
+          const int gq = g0 + (q / 3) * N + (q % 3);
+          acc0 += cf * X[gq];
+          acc1 += cf * X[gq + nv];
+        }
+      }
+    }
+    R[node] = B[node] - acc0;
+    R[node + nv] = B[node + nv] - acc1;
+  }
+  __syncthreads();
+}
+
 template <class T, int FL>
 __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __restrict__ Ainv, int m,
                                                         const T* __restrict__ bin, T* __restrict__ xout, T omega,
@@ -564,6 +604,19 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
     B[l] = sm + off; off += 2 * N * N;
     R[l] = sm + off; off += 2 * N * N;
   }
+  constexpr bool NODE = !(FL & QF_CONV);
+  __shared__ T KM[81], MK[81];
+  if (NODE) {
+    for (int k = threadIdx.x; k < 81; k += blockDim.x) {
+      const int i = k / 9, q = k % 9;
+      KM[k] = (T)(k1d(i % 3, q % 3) * m1d(i / 3, q / 3));
+      MK[k] = (T)(m1d(i % 3, q % 3) * k1d(i / 3, q / 3));
+    }
+  }
+  auto resid = [&](int l) {
+    if (NODE) cq2_residual_node<T>(L.n[l], L.hx[l], L.hy[l], L.nu[l], KM, MK, X[l], B[l], R[l]);
+    else cq2_residual<T, FL>(L.n[l], L.hx[l], L.hy[l], L.nu[l], L.sd[l], L.w[l], X[l], B[l], R[l]);
+  };
   {
     const int N = 2 * L.n[0] + 1;
     for (int k = threadIdx.x; k < 2 * N * N; k += blockDim.x) B[0][k] = bin[k];
@@ -577,11 +630,11 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
     }
     __syncthreads();
     for (int s = 1; s < pre; ++s) {
-      cq2_residual<T, FL>(n, L.hx[l], L.hy[l], L.nu[l], L.sd[l], L.w[l], X[l], B[l], R[l]);
+      resid(l);
       for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] += omega * L.dinv[l][k < nv ? k : k - nv] * R[l][k];
       __syncthreads();
     }
-    cq2_residual<T, FL>(n, L.hx[l], L.hy[l], L.nu[l], L.sd[l], L.w[l], X[l], B[l], R[l]);
+    resid(l);
     const int nc = L.n[l + 1], Nc = 2 * nc + 1, nvc = Nc * Nc;
     for (int node = threadIdx.x; node < nvc; node += blockDim.x) {
       const int J = node / Nc, I = node - J * Nc;
@@ -644,7 +697,7 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
     }
     __syncthreads();
     for (int s = 0; s < post; ++s) {
-      cq2_residual<T, FL>(n, L.hx[l], L.hy[l], L.nu[l], L.sd[l], L.w[l], X[l], B[l], R[l]);
+      resid(l);
       for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] += omega * L.dinv[l][k < nv ? k : k - nv] * R[l][k];
       __syncthreads();
     }
@@ -783,8 +836,10 @@ __global__ void k_q1_jr(int n, T hx, T hy, T omega, const T* __restrict__ dinv, 
 // Q1 prolongation fused with the smoothing sweep: x' = x + P xc ; y = x' + omega D^{-1} (b - K1 x')
 template <class T>
 __global__ void k_q1_ps(int n, T hx, T hy, T omega, const T* __restrict__ dinv, const T* __restrict__ b,
-                        const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ y, const int* done) {
+                        const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ y, const int* done,
+                        int sums, Slot sl, int soff) {
   if (done != nullptr && *done) return;
+  T s0 = 0, s1 = 0;
   const int M = n + 1, Mc = n / 2 + 1;
   const T rxy = hy / hx, ryx = hx / hy;
   auto xcorr = [&](int jj, int ii) -> T {
@@ -804,7 +859,16 @@ __global__ void k_q1_ps(int n, T hx, T hy, T omega, const T* __restrict__ dinv, 
         }
     })
     const T xv = xcorr(J, I);
-    y[node] = xv + omega * dinv[node] * (b[node] - acc);
+    const T yv = xv + omega * dinv[node] * (b[node] - acc);
+    y[node] = yv;
+    if (sums) {
+      s0 += yv;
+      s1 += (T)(((I > 0) + (I < n)) * ((J > 0) + (J < n))) * yv;
+    }
+  }
+  if (sums) {   // (sum y, sum_I (#elements at I) y_I, 0) for the M_Q constant
+    double v[3] = {(double)s0, (double)s1, 0.0};
+    if (slot_arrive<3>(sl, soff + blockIdx.x, v)) finish_slot_n<3>(sl, v);
   }
 }
 
@@ -932,7 +996,11 @@ template <class T>
 static eth_status q1_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, const int* done);
 
 template <class T>
-eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done, const T** result) {
+bool q1_vcycle_fused(const Hier<T>& H, int pre, int post) { return H.fused && pre == 1 && post == 1 && q1_fused_start(H) >= 1; }
+
+template <class T>
+eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done, const T** result,
+                          const Slot* sums, int soff) {
   const int nl = (int)H.lv.size();
   const T om = (T)H.omega;
   *result = H.lv[0].x;
@@ -952,7 +1020,9 @@ eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int*
       res[Lc] = H.lv[Lc].x;
       for (int l = Lc - 1; l >= 0; --l) {
         Level<T>& L = H.lv[l];
-        k_q1_ps<T><<<q1_blocks(L.n), 256, 0, g->s>>>(L.n, (T)L.hx, (T)L.hy, om, L.dinv, L.b, L.x, res[l + 1], L.t, done);
+        const bool s0 = (l == 0 && sums != nullptr);
+        k_q1_ps<T><<<q1_blocks(L.n), 256, 0, g->s>>>(L.n, (T)L.hx, (T)L.hy, om, L.dinv, L.b, L.x, res[l + 1], L.t, done,
+                                                     s0 ? 1 : 0, s0 ? *sums : Slot{}, soff);
         ETH_CUDA(cudaGetLastError());
         g->launches++;
         res[l] = L.t;
@@ -1171,7 +1241,8 @@ static int q1_fused_start(const Hier<T>& H) {
   template void mg_free<T>(Hier<T>&);                                                                    \
   template eth_status vcycle_vel<T>(eth_grid*, Hier<T>&, const double*, double*, int, int, const int*,   \
                                     const Slot*, int);                                                   \
-  template eth_status vcycle_q1_from<T>(eth_grid*, Hier<T>&, int, int, const int*, const T**);
+  template eth_status vcycle_q1_from<T>(eth_grid*, Hier<T>&, int, int, const int*, const T**, const Slot*, int); \
+  template bool q1_vcycle_fused<T>(const Hier<T>&, int, int);
 ETH_MG_INST(float)
 ETH_MG_INST(double)
 

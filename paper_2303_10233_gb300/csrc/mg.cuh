@@ -33,7 +33,11 @@ eth_status vcycle_vel(eth_grid* g, Hier<T>& H, const double* v, double* z, int p
 // Q1 V-cycle on level 0 whose b (and, for the unfused path, x after the first
 // sweep) are already set; *result points to the level-0 result (type T).
 template <class T>
-eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done, const T** result);
+eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int* done, const T** result,
+                          const Slot* sums = nullptr, int soff = 0);
+// true when vcycle_q1_from takes the fused path (and can fold the level-0 sums)
+template <class T>
+bool q1_vcycle_fused(const Hier<T>& H, int pre, int post);
 int vel_final_blocks(int n);
 
 }  // namespace eth

@@ -17,7 +17,13 @@
 
 namespace eth {
 
-constexpr int TEX = 32, TEY = 8;                 // computed elements per CTA
+#ifndef ETH_TEY
+#define ETH_TEY 8
+#endif
+#ifndef ETH_OUT_HWCVT
+#define ETH_OUT_HWCVT 0
+#endif
+constexpr int TEX = 32, TEY = ETH_TEY;           // computed elements per CTA
 constexpr int OEX = TEX - 1, OEY = TEY - 1;      // owned elements per CTA
 constexpr int Q2T = TEX * TEY;                   // threads per CTA (1 element each)
 constexpr int SQX = 2 * TEX + 1, SQY = 2 * TEY + 1;   // shared Q2 node tile
@@ -92,6 +98,17 @@ __host__ __device__ constexpr double g12(int d, int b) {
 }
 __host__ __device__ constexpr double c0v(int a) { return a == 0 ? -1.0 : (a == 1 ? 0.0 : 1.0); }
 __host__ __device__ constexpr double g0v(int b) { return b == 1 ? 4.0 / 6.0 : 1.0 / 6.0; }
+
+// FP32 -> FP64 of kernel outputs: the conversion instruction (FP64 pipe, idle in
+// FP32 element kernels) or the integer bit path (ALU pipe).
+template <class TO, class CT>
+__device__ __forceinline__ TO cvt_out(CT v) {
+#if ETH_OUT_HWCVT
+  return (TO)v;
+#else
+  return cvt<TO, CT>(v);
+#endif
+}
 
 template <class CT, int F>
 __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9], const CT (&P1)[4], CT P0,
@@ -459,14 +476,14 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
       if (EPI == EPI_APPLY) {
         if (bnd) {
           if (XIN) { o0 = (TO)P.x[g]; o1 = (TO)P.x[g + nv]; } else { o0 = 0; o1 = 0; }
-        } else { o0 = cvt<TO, CT>(s0); o1 = cvt<TO, CT>(s1); }
+        } else { o0 = cvt_out<TO, CT>(s0); o1 = cvt_out<TO, CT>(s1); }
       } else if (EPI == EPI_SMOOTH) {
         if (bnd) { if (P.bsrc) { o0 = (TO)P.bsrc[g]; o1 = (TO)P.bsrc[g + nv]; } else { o0 = 0; o1 = 0; } }
         else {
           const int sI = lj * SQX + li;
           const CT di = P.omega * P.dinv[g];
-          o0 = cvt<TO, CT>(sx[sI] + di * (P.b[g] - s0));
-          o1 = cvt<TO, CT>(sx[SQY * SQX + sI] + di * (P.b[g + nv] - s1));
+          o0 = cvt_out<TO, CT>(sx[sI] + di * (P.b[g] - s0));
+          o1 = cvt_out<TO, CT>(sx[SQY * SQX + sI] + di * (P.b[g + nv] - s1));
         }
       } else if (EPI == EPI_RESID) {
         if (bnd) { o0 = 0; o1 = 0; } else { o0 = (TO)(P.b[g] - s0); o1 = (TO)(P.b[g + nv] - s1); }
@@ -514,7 +531,7 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
       auto Q = [&](int cc, int dd, int t) -> CT { return eo[(18 + dd * 2 + cc) * Q2T + t]; };
       auto pemit = [&](int I, int J, CT v) {
         const size_t gp = (size_t)J * (n + 1) + I;
-        const TO so = cvt<TO, CT>(v);
+        const TO so = cvt_out<TO, CT>(v);
         P.yp[gp] = so;
         if (DOT) dacc += (double)so * (double)P.dvp[gp];
       };
@@ -524,7 +541,7 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
       if (ex == n - 1 && ey == n - 1) pemit(ex + 1, ey + 1, Q(1, 1, tid));
       if (HP0) {
         const size_t ge = (size_t)n1 + (size_t)ey * n + ex;
-        const TO so = cvt<TO, CT>(eo[22 * Q2T + tid]);
+        const TO so = cvt_out<TO, CT>(eo[22 * Q2T + tid]);
         P.yp[ge] = so;
         if (DOT) dacc += (double)so * (double)P.dvp[ge];
       }

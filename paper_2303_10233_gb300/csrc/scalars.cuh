@@ -35,6 +35,7 @@ enum : int {
   S_MQNU,                      // pressure block factor (nu)
   S_ITS,                       // iterations done (as double)
   S_INNER_TOL, S_RZ, S_RZ0, S_ALPHA, S_BETACG,   // inner PCG
+  S_WXP,                       // 1 while the w/x update of the last Givens step is pending
   S_LAST
 };
 
@@ -50,6 +51,7 @@ enum : int {
   FIN_PCG_ALPHA,      // alpha = rz / <p, A p>
   FIN_PCG_RZ,         // beta = rz_new / rz; rz = rz_new
   FIN_PCG_RR,         // <r, r> <= target -> inner done
+  FIN_VWX,            // beta from the v sums; done = pending once the pending w/x update is applied
 };
 
 __device__ __forceinline__ void finish_minres_gamma(Scalars* sc, double g2) {
@@ -75,6 +77,7 @@ __device__ __forceinline__ void finish_minres_gamma(Scalars* sc, double g2) {
   v[S_CPREV] = v[S_C]; v[S_C] = cn;
   v[S_SPREV] = v[S_S]; v[S_S] = sn;
   v[S_ITS] += 1.0;
+  v[S_WXP] = 1.0;
   if (fabs(v[S_ETA]) < v[S_TOL] * v[S_ETA1]) v[S_PEND] = 1.0;
   if (!isfinite(v[S_ETA])) { v[S_PEND] = 1.0; sc->status = 8; }
 }
@@ -111,6 +114,14 @@ __device__ __forceinline__ void finish_slot_n(const Slot& sl, const double (&s)[
       break;
     case FIN_VSUMS:
       v[S_BETA] = (s[0] - s[1]) / (v[S_NP1] + v[S_NP0]);
+      break;
+    case FIN_VWX:
+      v[S_BETA] = (s[0] - s[1]) / (v[S_NP1] + v[S_NP0]);
+      if (v[S_WXP] != 0.0) {
+        v[S_WXP] = 0.0;
+        if (v[S_PEND] != 0.0) sc->done = 1;
+      }
+      sc->iter += 1;
       break;
     case FIN_MQ: {
       // z_k = c z~ + g1, z_0 = (v0+beta)/|T| - (c/4) sum_T z~ - g1 ; choose g1 so k^T z = 0

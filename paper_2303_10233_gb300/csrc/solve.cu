@@ -141,6 +141,47 @@ __global__ void k_minres_wx(size_t nt, const double* __restrict__ zj, double* __
   if (slot_arrive<1>(sl, blockIdx.x, v)) finish_slot(sl, 0.0);
 }
 
+// Fused MINRES vector update of iteration j: v_{j+1} = VA K z_j - VB v_j - VC v_{j-1}
+// (into vo, with the sums of its p1 / p0 blocks) and, when the previous Givens
+// step left it pending, its w/x update w_j = WZ z_{j-1} - WO w_{j-2} - WW w_{j-1}
+// (into wold), x += XC w_j.  The last block sets done once a converged step's
+// update has been applied.
+__global__ void k_minres_vwx(size_t nt, size_t nu2, size_t n1, const double* __restrict__ Kz, const double* __restrict__ vj,
+                             double* __restrict__ vo, const double* __restrict__ zprev, double* __restrict__ wold,
+                             const double* __restrict__ wcur, double* __restrict__ x, Scalars* __restrict__ sc, Slot sl) {
+  if (sc->done) return;
+  const double a = sc->v[S_VA], b = sc->v[S_VB], c = sc->v[S_VC];
+  const bool wx = sc->v[S_WXP] != 0.0;
+  const double cz = sc->v[S_WZ], co = sc->v[S_WO], cw = sc->v[S_WW], cx = sc->v[S_XC];
+  double a1 = 0.0, a0 = 0.0;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
+    const double v = a * Kz[k] - b * vj[k] - c * vo[k];
+    vo[k] = v;
+    if (k >= nu2) { if (k < nu2 + n1) a1 += v; else a0 += v; }
+    if (wx) {
+      const double w = cz * zprev[k] - co * wold[k] - cw * wcur[k];
+      wold[k] = w;
+      x[k] += cx * w;
+    }
+  }
+  double v[2] = {a1, a0};
+  if (slot_arrive<2>(sl, blockIdx.x, v)) finish_slot_n<2>(sl, v);
+}
+
+// the w/x update left pending when the iteration loop stops (applied iff pending)
+__global__ void k_minres_wx_tail(size_t nt, const double* __restrict__ zj, double* __restrict__ wo, const double* __restrict__ wj,
+                                 double* __restrict__ x, Scalars* __restrict__ sc) {
+  if (sc->v[S_WXP] == 0.0) return;
+  const double cz = sc->v[S_WZ], co = sc->v[S_WO], cw = sc->v[S_WW], cx = sc->v[S_XC];
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
+    const double w = cz * zj[k] - co * wo[k] - cw * wj[k];
+    wo[k] = w;
+    x[k] += cx * w;
+  }
+}
+
+__global__ void k_minres_wx_clear(Scalars* sc) { sc->v[S_WXP] = 0.0; }
+
 __global__ void k_init_scalars(Scalars* sc, double tol, double n1, double n0, double mqc, double nu) {
   for (int k = 0; k < S_LAST; ++k) sc->v[k] = 0.0;
   sc->v[S_TOL] = tol;
@@ -163,7 +204,8 @@ __global__ void k_init_scalars(Scalars* sc, double tol, double n1, double n0, do
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_mq_t(int n, const double* __restrict__ vp, const Scalars* __restrict__ sc, T* __restrict__ b,
-                       T* __restrict__ x, const T* __restrict__ dinv, T omega, const int* done) {
+                       T* __restrict__ x, const T* __restrict__ dinv, T omega, const int* done,
+                       int sums, Slot sl, T inv_area) {
   if (done != nullptr && *done) return;
   const int M = n + 1, n1 = M * M;
   const T beta = (T)sc->v[S_BETA];
@@ -174,6 +216,13 @@ __global__ void k_mq_t(int n, const double* __restrict__ vp, const Scalars* __re
     const T t = cvt<T, double>(vp[node]) - beta - T(0.25) * s;
     b[node] = t;
     x[node] = omega * dinv[node] * t;
+  }
+  if (sums) {   // (0, 0, sum_T (v0_T + beta)/|T|) for the M_Q constant
+    T s2 = 0;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x)
+      s2 += (cvt<T, double>(vp[n1 + e]) + beta) * inv_area;
+    double v[3] = {0.0, 0.0, (double)s2};
+    if (slot_arrive<3>(sl, blockIdx.x, v)) finish_slot_n<3>(sl, v);
   }
 }
 
@@ -232,18 +281,26 @@ eth_status precond_pressure(eth_grid* g, Hier<T>& Q, const double* vp, double* z
   Level<T>& L0 = Q.lv[0];
   const cudaStream_t keep = g->s;
   g->s = s;
-  k_mq_t<T><<<vblocks(g->n1), 256, 0, s>>>(g->n, vp, g->sc, L0.b, L0.x, L0.dinv, (T)Q.omega, done);
+  const int nbt = vblocks(g->n1), nbp = (int)q1_blocks(g->n);
+  const T inv_area = (T)(1.0 / (g->hx * g->hy));
+  const bool fold = q1_vcycle_fused<T>(Q, 1, 1);
+  const int nb = mq_blocks(g);
+  // the three sums of the M_Q constant come from k_mq_t (P0 part) and the last
+  // Q1 smoothing sweep (Q1 part) when the fused V-cycle runs, else from k_mq_sums
+  Slot sm = slot_of(g, SL_MQ, fold ? nbt + nbp : nb, FIN_MQ);
+  k_mq_t<T><<<nbt, 256, 0, s>>>(g->n, vp, g->sc, L0.b, L0.x, L0.dinv, (T)Q.omega, done, fold ? 1 : 0, sm, inv_area);
   ETH_CUDA(cudaGetLastError());
   const T* zt = nullptr;
-  eth_status st = vcycle_q1_from<T>(g, Q, 1, 1, done, &zt);
+  eth_status st = vcycle_q1_from<T>(g, Q, 1, 1, done, &zt, fold ? &sm : nullptr, nbt);
   if (st != ETH_OK) { g->s = keep; return st; }
-  const int nb = mq_blocks(g);
-  Slot sm = slot_of(g, SL_MQ, nb, FIN_MQ);
-  k_mq_sums<T><<<nb, 256, 0, s>>>(g->n, zt, vp, (T)(1.0 / (g->hx * g->hy)), sm, done);
+  if (!fold) {
+    k_mq_sums<T><<<nb, 256, 0, s>>>(g->n, zt, vp, inv_area, sm, done);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+  }
+  k_mq_out<T><<<nb, 256, 0, s>>>(g->n, zt, vp, zp, inv_area, g->sc, gsl, goff, done);
   ETH_CUDA(cudaGetLastError());
-  k_mq_out<T><<<nb, 256, 0, s>>>(g->n, zt, vp, zp, (T)(1.0 / (g->hx * g->hy)), g->sc, gsl, goff, done);
-  ETH_CUDA(cudaGetLastError());
-  g->launches += 3;
+  g->launches += 2;
   g->s = keep;
   return ETH_OK;
 }
@@ -547,12 +604,13 @@ static eth_status minres_iter(eth_grid* g, Work* w, const eth_opts* o, bool fp32
   double* wo = w->W[(j + 1) & 1];
   ETH_TRY(op_apply_K_dot(g, fp32, false, zj, w->Kz, slot_of(g, SL_DELTA, 0, FIN_MINRES_DELTA), done));
   const int nb = vblocks(nt);
-  k_minres_v<<<nb, 256, 0, g->s>>>(nt, nu2, (size_t)g->n1, w->Kz, vj, vo, g->sc, slot_of(g, SL_VSUM, nb, FIN_VSUMS));
+  // v_{j+1} and the pending w/x update of iteration j-1 (z_{j-1} = zn's buffer, not yet overwritten)
+  k_minres_vwx<<<nb, 256, 0, g->s>>>(nt, nu2, (size_t)g->n1, w->Kz, vj, vo, zn, wj, wo, w->d, g->sc,
+                                     slot_of(g, SL_VSUM, nb, FIN_VWX));
   ETH_CUDA(cudaGetLastError());
   ETH_TRY(precond_stokes<T>(g, w, o, vo, zn, FIN_MINRES_GAMMA, done));
-  k_minres_wx<<<nb, 256, 0, g->s>>>(nt, zj, wo, wj, w->d, g->sc, slot_of(g, SL_DONE, nb, FIN_DONE));
-  ETH_CUDA(cudaGetLastError());
-  g->launches += 2;
+  g->launches += 1;
+  (void)wo;
   return ETH_OK;
 }
 
@@ -618,6 +676,13 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
     j += 2;
     ETH_TRY(read_scalars(g));
     if (g->sch->done || (int)g->sch->v[S_ITS] >= maxit) break;
+  }
+  {
+    const int J = (int)g->sch->v[S_ITS];   // last iteration with a Givens step
+    k_minres_wx_tail<<<vblocks(nt), 256, 0, g->s>>>(nt, w->Z[J & 1], w->W[(J + 1) & 1], w->W[J & 1], w->d, g->sc);
+    k_minres_wx_clear<<<1, 1, 0, g->s>>>(g->sc);
+    ETH_CUDA(cudaGetLastError());
+    g->launches += 2;
   }
   *its = (int)g->sch->v[S_ITS];
   *dstat = g->sch->status;
