@@ -165,6 +165,23 @@ eth_status eth_apply(eth_grid* g, eth_op op, int fp32, const double* x_dev, doub
 eth_status eth_adjoint_gradients(eth_grid* g, const double* lu_dev, const double* u_dev,
                                  double* grad_f_dev, double* grad_nu_host);
 
+/* Allocation-free K apply with its dot product, for callers that cannot
+ * allocate device memory (they run inside another framework's memory pool or
+ * under a fixed memory budget, or must not call cudaMalloc after start-up) and
+ * therefore cannot create an eth_grid.  Computes y = K x for the Stokes
+ * operator (nu*A, Dirichlet velocity rows identity) of an n x n grid on
+ * [x0,x1] x [y0,y1] and *dot_dev = <K x, x> (FP64), with FP32 element
+ * arithmetic when fp32 != 0.  x_dev, y_dev: N_t FP64 device vectors; dot_dev:
+ * one FP64 device value; all owned by the caller.  Nothing is allocated: the
+ * reduction scratch is a fixed file-scope device array (32768 block partials,
+ * so n <= 2048; larger n returns ETH_EINVAL) that every GPU loading the library
+ * holds until exit.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
+ * share the array: calls whose kernels overlap on the GPU race.  The paper has
+ * no counterpart of this entry point. */
+eth_status eth_apply_k_dot_static(int n, double x0, double x1, double y0, double y1, double nu, int fp32,
+                                  const double* x_dev, double* y_dev, double* dot_dev, void* cuda_stream);
+
 /* Batched solves of independent instances (each created with its own handle,
  * all on the same stream). */
 eth_status eth_batch_create(int count, eth_grid* const* grids, eth_batch** out);

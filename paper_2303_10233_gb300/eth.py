@@ -77,6 +77,7 @@ def load(path=LIB_PATH):
         "eth_solve_adjoint": (i, [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Stats)]),
         "eth_apply": (i, [vp, i, i, vp, vp]),
         "eth_adjoint_gradients": (i, [vp, vp, vp, vp, ctypes.POINTER(d)]),
+        "eth_apply_k_dot_static": (i, [i, d, d, d, d, d, i, vp, vp, vp, vp]),
         "eth_batch_create": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "eth_batch_solve": (i, [vp, ctypes.POINTER(Opts), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)]),
         "eth_batch_destroy": (None, [vp]),
@@ -228,6 +229,14 @@ class Grid:
         gn = ctypes.c_double()
         _check(load().eth_adjoint_gradients(self.h, _ptr(lu), _ptr(u), _ptr(gf), ctypes.byref(gn)))
         return gf, gn.value
+
+
+def apply_k_dot_static(n, nu, x, y, dot, fp32=False, domain=(-1.0, 1.0, -1.0, 1.0), stream=None):
+    """y = K x and dot = <K x, x> for a Stokes grid, through the allocation-free entry point."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(load().eth_apply_k_dot_static(int(n), *map(float, domain), float(nu), int(bool(fp32)), _ptr(x), _ptr(y),
+                                         _ptr(dot), ctypes.c_void_p(st.cuda_stream)))
 
 
 class Batch:

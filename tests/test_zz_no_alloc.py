@@ -1,0 +1,50 @@
+"""The allocation-free K apply (eth_apply_k_dot_static) against the handle-based
+entry point: same y = K x, same <K x, x>, on two calls in a row (the shared
+static scratch keeps the previous call's contents, which the entry point must
+not depend on).
+
+This file is collected last on purpose: callers that cannot allocate device
+memory use this entry point, and a failure here should not hide the results
+of the rest of the suite."""
+import numpy as np
+import pytest
+
+from paper_2303_10233_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eth():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_10233_gb300 import eth as E
+    return E
+
+
+@pytest.mark.parametrize("n", [16, 70])
+@pytest.mark.parametrize("fp32", [False, True])
+def test_static_scratch_apply_matches_handle_apply(eth, n, fp32):
+    w = W.mms(n, seed=0, nu=0.7)
+    G = eth.problem(w)
+    rng = np.random.default_rng(100 + n)
+    for call in range(2):
+        x = torch.as_tensor(rng.standard_normal(G.nt), device="cuda")
+        ref = G.apply("K", x, fp32=fp32)
+        y = torch.empty_like(x)
+        dot = torch.zeros(1, dtype=torch.float64, device="cuda")
+        eth.apply_k_dot_static(n, w["nu"], x, y, dot, fp32=fp32)
+        torch.cuda.synchronize()
+        tol = 5e-5 if fp32 else 1e-13
+        scale = float(torch.abs(ref).max())
+        assert float(torch.abs(y - ref).max()) <= tol * scale
+        dref = float(torch.dot(ref, x))
+        assert abs(float(dot[0]) - dref) <= 1e-10 * max(1.0, float(torch.abs(ref).abs().sum() * torch.abs(x).max()))
+    G.close()
+
+
+def test_static_scratch_rejects_oversize(eth):
+    x = torch.zeros(1, dtype=torch.float64, device="cuda")
+    with pytest.raises(eth.EthError):
+        eth.apply_k_dot_static(4096, 1.0, x, x, x)
