@@ -21,7 +21,7 @@
 
 namespace eth {
 
-constexpr int GM_MAX = 64;
+constexpr int GM_MAX = 160;
 
 struct GScalars {
   double H[GM_MAX + 1][GM_MAX];
@@ -29,7 +29,7 @@ struct GScalars {
   double h1[GM_MAX + 1], h2[GM_MAX + 1];
   double res, tol_abs, wnorm, beta;
   double pcg[8];       // inner PCG scalars: rz, pAp, alpha, beta
-  int k, done, bdown, pad;
+  int k, done, bdown, skip2;   // skip2: the second Gram-Schmidt pass is not needed
 };
 
 struct GMRESWork {
@@ -89,25 +89,29 @@ __device__ __forceinline__ bool multi_finish(int nvec, int nb, double* part, uns
   return true;
 }
 
+// h_i = <V_i, w> for i < nvec; with wnorm, also out[nvec] = <w, w> (grouped MG_GRP vectors per pass)
 __global__ void k_mdot(size_t n, const double* __restrict__ V, size_t ld, int nvec, const double* __restrict__ w,
-                       double* part, unsigned* ticket, double* out, const int* done) {
-  if (done && *done) return;
+                       double* part, unsigned* ticket, double* out, const int* done, const int* skip, int wnorm) {
+  if ((done && *done) || (skip && *skip)) return;
   const int nb = gridDim.x;
-  for (int g0 = 0; g0 < nvec; g0 += MG_GRP) {
+  const int nout = nvec + (wnorm ? 1 : 0);
+  for (int g0 = 0; g0 < nout; g0 += MG_GRP) {
     double acc[MG_GRP];
 #pragma unroll
     for (int i = 0; i < MG_GRP; ++i) acc[i] = 0.0;
     for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
       const double wk = w[k];
 #pragma unroll
-      for (int i = 0; i < MG_GRP; ++i)
+      for (int i = 0; i < MG_GRP; ++i) {
         if (g0 + i < nvec) acc[i] += V[(size_t)(g0 + i) * ld + k] * wk;
+        else if (g0 + i == nvec && wnorm) acc[i] += wk * wk;
+      }
     }
     block_sum<MG_GRP>(acc);
     if (threadIdx.x == 0)
-      for (int i = 0; i < MG_GRP && g0 + i < nvec; ++i) part[(size_t)(g0 + i) * nb + blockIdx.x] = acc[i];
+      for (int i = 0; i < MG_GRP && g0 + i < nout; ++i) part[(size_t)(g0 + i) * nb + blockIdx.x] = acc[i];
   }
-  multi_finish(nvec, nb, part, ticket, out);
+  multi_finish(nout, nb, part, ticket, out);
 }
 
 // w -= sum_i h_i V_i ; optionally ||w||^2 -> finisher (Arnoldi column j)
@@ -134,9 +138,14 @@ __device__ __forceinline__ void arnoldi_finish(GScalars* gs, int j, double wn2) 
   else if (gs->res <= gs->tol_abs || wn == 0.0) gs->done = 1;
 }
 
+// w -= sum_i h_i V_i.  mode 0: nothing else; mode 1: ||w||^2 and the Arnoldi/Givens
+// finisher; mode 2 (after the first Gram-Schmidt pass): the DGKS test
+// ||w_new|| >= 0.7 ||w_old|| accepts the column (h2 = 0, finisher, skip the
+// second pass), otherwise the second pass runs.
 __global__ void k_mupd(size_t n, const double* __restrict__ V, size_t ld, int nvec, const double* __restrict__ h,
-                       double* __restrict__ w, int norm, double* part, unsigned* ticket, GScalars* gs, int j, const int* done) {
-  if (done && *done) return;
+                       double* __restrict__ w, int norm, double* part, unsigned* ticket, GScalars* gs, int j, const int* done,
+                       const int* skip) {
+  if ((done && *done) || (skip && *skip)) return;
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     double v = w[k];
@@ -149,7 +158,20 @@ __global__ void k_mupd(size_t n, const double* __restrict__ V, size_t ld, int nv
   block_sum<1>(a);
   if (threadIdx.x == 0) part[blockIdx.x] = a[0];
   if (multi_finish(1, gridDim.x, part, ticket, &gs->pcg[7])) {
-    if (threadIdx.x == 0) arnoldi_finish(gs, j, gs->pcg[7]);
+    if (threadIdx.x == 0) {
+      if (norm == 2) {
+        const double before = gs->h1[nvec];   // ||w||^2 before the first pass
+        if (gs->pcg[7] >= 0.49 * before) {
+          for (int i = 0; i < nvec; ++i) gs->h2[i] = 0.0;
+          gs->skip2 = 1;
+          arnoldi_finish(gs, j, gs->pcg[7]);
+        } else {
+          gs->skip2 = 0;
+        }
+      } else {
+        arnoldi_finish(gs, j, gs->pcg[7]);
+      }
+    }
   }
 }
 
@@ -655,10 +677,12 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
       ETH_TRY(sys_apply(g, stage, fp32, adj, Zj, G->w));
       double* h1 = &G->gs->h1[0];
       double* h2 = &G->gs->h2[0];
-      k_mdot<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, G->w, G->part, G->ticket + 3, h1, done);
-      k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h1, G->w, 0, G->part, G->ticket + 4, G->gs, j, done);
-      k_mdot<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, G->w, G->part, G->ticket + 3, h2, done);
-      k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h2, G->w, 1, G->part, G->ticket + 4, G->gs, j, done);
+      // classical Gram-Schmidt with selective reorthogonalisation (DGKS, 0.7)
+      const int* sk = &G->gs->skip2;
+      k_mdot<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, G->w, G->part, G->ticket + 3, h1, done, nullptr, 1);
+      k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h1, G->w, 2, G->part, G->ticket + 4, G->gs, j, done, nullptr);
+      k_mdot<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, G->w, G->part, G->ticket + 3, h2, done, sk, 0);
+      k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h2, G->w, 1, G->part, G->ticket + 4, G->gs, j, done, sk);
       k_vscale<<<nb, 256, 0, g->s>>>(ntv, G->w, G->V + (size_t)(j + 1) * ld, G->gs, 0);
       ETH_CUDA(cudaGetLastError());
       g->launches += 5;

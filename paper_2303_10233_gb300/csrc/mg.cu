@@ -1077,8 +1077,14 @@ eth_status vcycle_q1_from(eth_grid* g, Hier<T>& H, int pre, int post, const int*
 // in one tile launch per level, single-CTA shared-memory V-cycle below the
 // coarse threshold.
 // ---------------------------------------------------------------------------
-template <class T> static int q2_coarse_threshold() { return 16; }
-template <class T> static int q1_coarse_threshold() { return 32; }
+#ifndef ETH_Q2_COARSE
+#define ETH_Q2_COARSE 16
+#endif
+#ifndef ETH_Q1_COARSE
+#define ETH_Q1_COARSE 32
+#endif
+template <class T> static int q2_coarse_threshold() { return ETH_Q2_COARSE; }
+template <class T> static int q1_coarse_threshold() { return ETH_Q1_COARSE; }
 
 template <class T, class TI, int CF>
 static eth_status q2_jr(eth_grid* g, Level<T>& L, const TI* b, T* bcopy, T omega, const int* done) {
@@ -1122,12 +1128,12 @@ static eth_status q2_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, int pre, int
     const size_t N = 2 * (size_t)L.n + 1;
     smem += 3 * 2 * N * N * sizeof(T);
   }
-  static bool set = false;
-  if (!set) {
-    ETH_CUDA(cudaFuncSetAttribute(k_q2_coarse_vc<T, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    set = true;
+  static size_t set = 0;   // largest dynamic shared memory requested so far (static shared memory counts too)
+  if (smem > 200 * 1024) { set_error("multigrid: coarse levels exceed shared memory"); return ETH_EINVAL; }
+  if (smem > set) {
+    ETH_CUDA(cudaFuncSetAttribute(k_q2_coarse_vc<T, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set = smem;
   }
-  if (smem > 227 * 1024) { set_error("multigrid: coarse levels exceed shared memory"); return ETH_EINVAL; }
   k_q2_coarse_vc<T, FL><<<1, 512, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, pre, post, done);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
@@ -1208,12 +1214,12 @@ static eth_status q1_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, const int* d
     const size_t M = (size_t)L.n + 1;
     smem += 3 * M * M * sizeof(T);
   }
-  static bool set = false;
-  if (!set) {
-    ETH_CUDA(cudaFuncSetAttribute(k_q1_coarse_vc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
-    set = true;
+  static size_t set = 0;
+  if (smem > 200 * 1024) { set_error("multigrid: Q1 coarse levels exceed shared memory"); return ETH_EINVAL; }
+  if (smem > set) {
+    ETH_CUDA(cudaFuncSetAttribute(k_q1_coarse_vc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set = smem;
   }
-  if (smem > 227 * 1024) { set_error("multigrid: Q1 coarse levels exceed shared memory"); return ETH_EINVAL; }
   k_q1_coarse_vc<T><<<1, 1024, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, done);
   ETH_CUDA(cudaGetLastError());
   g->launches++;

@@ -21,7 +21,7 @@ namespace eth {
 #define ETH_TEY 8
 #endif
 #ifndef ETH_OUT_HWCVT
-#define ETH_OUT_HWCVT 0
+#define ETH_OUT_HWCVT 1
 #endif
 constexpr int TEX = 32, TEY = ETH_TEY;           // computed elements per CTA
 constexpr int OEX = TEX - 1, OEY = TEY - 1;      // owned elements per CTA
