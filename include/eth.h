@@ -80,13 +80,24 @@ typedef struct {
   double c_stage;          /* two-stage factor c (Sec. 3.1), Step I to c*tol */
   int precision;           /* eth_precision                                  */
   int mg_pre, mg_post;     /* smoothing sweeps of the velocity V-cycle       */
-  int mg_min_n;            /* coarsest grid size of the hierarchies          */
+  int mg_min_n;            /* coarsest grid size of the hierarchies (dense
+                              solve there); 0: 4 for Stokes, 8 for Oseen     */
   int mq_mode;             /* eth_mq_mode                                    */
   int a_exact;             /* 1: exact velocity solves (inner PCG), P_1 form */
   double inner_tol;        /* inner exact-solve tolerance when exact         */
   double refine_inner_tol; /* mixed: relative tolerance of each inner solve  */
   int graph;               /* 1: replay captured CUDA graphs                 */
   int verbose;
+  int autotune;            /* 1: before the first solve of a grid, time the
+                              fused K apply with tiles of 32 x {4, 8, 16}
+                              elements per CTA and the persistent 32 x 8 form
+                              (mixed precision) and keep the fastest (cached
+                              per grid size, operator and precision for the
+                              process); 0: 32 x 8, one tile per CTA          */
+  int restart_max;         /* GMRES: when a restart cycle reduces the FP64
+                              residual by less than a factor 2, the next
+                              cycles use twice the restart length, up to
+                              restart_max (<= 160); 0 or <= restart: fixed  */
 } eth_opts;
 
 typedef struct {
@@ -98,6 +109,12 @@ typedef struct {
   double alg_bytes;        /* algorithmic bytes moved (estimate)             */
   int status;              /* eth_status of the solve                        */
   int kernel_launches;     /* device kernels launched by the solve           */
+  int escalations;         /* GMRES restart cycles that switched the Arnoldi
+                              products of a mixed-precision solve to FP64
+                              because the FP64 residual had grown (0 or 1 per
+                              stage)                                         */
+  int tile_rows;           /* element rows per tile of the fused K apply used */
+  int tile_persistent;     /* 1: its persistent pipelined form was used       */
 } eth_stats;
 
 /* Sizes of an n x n grid: N_v = (2n+1)^2, N_1 = (n+1)^2, N_0 = n^2.
@@ -113,6 +130,19 @@ void eth_default_opts(eth_opts* o);
 eth_status eth_grid_create(int n, double x0, double x1, double y0, double y1,
                            eth_kind kind, void* cuda_stream, eth_grid** out);
 void eth_grid_destroy(eth_grid* g);
+
+/* Pins the tile of the fused K apply: 32 x rows elements per CTA, rows in
+ * {4, 8, 16}, one tile per CTA; or, with persistent != 0 (rows = 8), a grid of
+ * resident CTAs that walk over the tiles and copy the next tile's input
+ * (cp.async) while computing the current one (FP32 element arithmetic only;
+ * FP64 applies use 32 x 8 one tile per CTA).  Turns the autotuner off for this
+ * grid; rows = 0 restores the default and lets the next solve with
+ * opts.autotune tune again.  Every apply gives bitwise the same K x whatever
+ * the tile (each node sums its element contributions in one fixed order);
+ * reductions group their partial sums by CTA.  ETH_EINVAL for other values or
+ * when the shape needs more reduction partials than the grid holds.  The paper
+ * has no counterpart. */
+eth_status eth_grid_set_tile(eth_grid* g, int rows, int persistent);
 
 /* Viscosity nu > 0 and, for ETH_OSEEN, the nodal Q2 wind w (device, 2*N_v
  * FP64, Sec. 3 "discrete wind w_h"); wind_dev must be NULL for ETH_STOKES.

@@ -67,13 +67,14 @@ void eth_default_opts(eth_opts* o) {
   o->precision = ETH_MIXED;
   o->mg_pre = 1;
   o->mg_post = 1;
-  o->mg_min_n = 4;
+  o->mg_min_n = 0;
   o->mq_mode = ETH_MQ_VCYCLE;
   o->a_exact = 0;
   o->inner_tol = 1e-12;
   o->refine_inner_tol = 1e-4;
   o->graph = 1;
   o->verbose = 0;
+  o->autotune = 1;
 }
 
 eth_status eth_grid_create(int n, double x0, double x1, double y0, double y1, eth_kind kind, void* cuda_stream,

@@ -73,10 +73,54 @@ __device__ __forceinline__ double f32_to_f64_bits(float f) {
   return __hiloint2double((int)hi, (int)lo);
 }
 
+// The same rounding with a shorter common path.  Adding 2^28 to the 64-bit
+// pattern rounds half up at the first dropped bit (the carry runs into the
+// exponent); bits 60..29 then hold the low nine exponent bits and the 23 kept
+// mantissa bits, and adding 128 to that nine-bit exponent field (mod 2^9) is
+// the rebias 1023 -> 127 for every exponent of the normal binary32 range.
+// Values outside that range (zero, binary32 subnormals, overflow, inf, NaN)
+// take the full conversion above on the lanes that need it.
+__device__ __forceinline__ float f64_to_f32_fast(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32);
+  const unsigned t = (unsigned)((u + (1ull << 28)) >> 29) + 0x40000000u;
+  const unsigned bits = (t & 0x7fffffffu) | (hi & 0x80000000u);
+  const unsigned ea = hi & 0x7ff00000u;
+  if (ea - (897u << 20) >= (254u << 20)) return f64_to_f32_bits(x);
+  return __uint_as_float(bits);
+}
+
+// Warp-collective form for staged loads: lanes with valid == false yield 0
+// without a conversion, and the full conversion runs only when some lane of
+// the warp holds a value outside the normal binary32 range.  Every lane of
+// the warp must call it (full mask).
+__device__ __forceinline__ float f64_to_f32_warp(double x, bool valid) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(u >> 32);
+  const unsigned t = (unsigned)((u + (1ull << 28)) >> 29) + 0x40000000u;
+  const unsigned bits = (t & 0x7fffffffu) | (hi & 0x80000000u);
+  const bool out = valid && ((hi & 0x7ff00000u) - (897u << 20) >= (254u << 20));
+  float r = valid ? __uint_as_float(bits) : 0.0f;
+  if (__any_sync(0xffffffffu, out)) {
+    if (out) r = f64_to_f32_bits(x);
+  }
+  return r;
+}
+
+#ifndef ETH_IN_FASTCVT
+#define ETH_IN_FASTCVT 1
+#endif
+
 template <class TO, class TI>
 __device__ __forceinline__ TO cvt(TI v) { return (TO)v; }
 template <>
-__device__ __forceinline__ float cvt<float, double>(double v) { return f64_to_f32_bits(v); }
+__device__ __forceinline__ float cvt<float, double>(double v) {
+#if ETH_IN_FASTCVT
+  return f64_to_f32_fast(v);
+#else
+  return f64_to_f32_bits(v);
+#endif
+}
 template <>
 __device__ __forceinline__ double cvt<double, float>(float v) { return f32_to_f64_bits(v); }
 

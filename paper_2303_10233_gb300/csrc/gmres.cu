@@ -643,16 +643,25 @@ static eth_status sys_apply(eth_grid* g, int stage, bool fp32, bool trans, const
 }
 
 template <class T>
+// Restarted flexible GMRES; every cycle starts from the FP64 residual of the
+// current iterate (a refinement step).  In mixed precision the Arnoldi
+// products K z run in FP32; a cycle can then only reduce the FP64 residual
+// as far as the FP32 products represent K z, and when the preconditioned
+// vectors z are large against K z (poor preconditioning at high cell Peclet
+// number) the FP64 residual can even grow.  After such a cycle the products
+// of the remaining cycles run in FP64 (*escalated = 1).
 static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, bool adj, const double* b, double* x,
-                            size_t ntv, double tol_abs, int maxit, int* its_out, double* res_out, int* status) {
+                            size_t ntv, double tol_abs, int maxit, int* its_out, double* res_out, int* status,
+                            int* escalated) {
   GMRESWork* G = w->gm;
-  const int m = G->m;
+  int m = std::max(1, std::min(o->restart, G->m));   // cycle length (adaptive up to G->m)
   const size_t ld = G->cap;
-  const bool fp32 = o->precision == ETH_MIXED;
+  bool fp32 = o->precision == ETH_MIXED;
   const int nb = gb(ntv);
   int its = 0;
   *status = 0;
-  double res = 0.0;
+  *escalated = 0;
+  double res = 0.0, res_prev = -1.0;
   while (true) {
     ETH_TRY(sys_apply(g, stage, false, adj, x, G->w));
     k_gm_resid<<<nb, 256, 0, g->s>>>(ntv, b, G->w, G->V, G->part, G->ticket, G->gs, tol_abs);
@@ -664,6 +673,16 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
     if (o->verbose) fprintf(stderr, "[eth] stage %d restart: its %d res %.3e (tol %.3e)\n", stage, its, res, tol_abs);
     if (!std::isfinite(res)) { *status = ETH_ENAN; break; }
     if (res <= tol_abs || its >= maxit) break;
+    if (fp32 && res_prev >= 0.0 && res > res_prev) {
+      fp32 = false;
+      *escalated = 1;
+      if (o->verbose) fprintf(stderr, "[eth] stage %d: FP64 residual grew, Arnoldi products now FP64\n", stage);
+    }
+    if (res_prev >= 0.0 && res > 0.5 * res_prev && m < G->m) {
+      m = std::min(2 * m, G->m);
+      if (o->verbose) fprintf(stderr, "[eth] stage %d: slow restart cycle, restart length now %d\n", stage, m);
+    }
+    res_prev = res;
     k_vscale<<<nb, 256, 0, g->s>>>(ntv, G->V, G->V, G->gs, 1);
     ETH_CUDA(cudaGetLastError());
     g->launches++;
@@ -737,10 +756,10 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
   const double nbred = std::sqrt(std::max(G->gsh->pcg[0] - G->gsh->pcg[1], 0.0));
   if (!(nb2 > 0.0)) { ETH_CUDA(cudaMemsetAsync(w->x, 0, nt * 8, g->s)); st->relres_true = 0; return ETH_OK; }
   const double eta = o->tol;
-  int its1 = 0, its2 = 0, s1 = 0, s2 = 0;
+  int its1 = 0, its2 = 0, s1 = 0, s2 = 0, e1 = 0, e2 = 0;
   double res1 = 0, res2 = 0;
   // Step I: reduced system on [u; p1], p0 = 0
-  ETH_TRY(gmres_run<T>(g, w, o, 1, adj, b, w->x, nt1, o->c_stage * eta * nbred, o->maxit, &its1, &res1, &s1));
+  ETH_TRY(gmres_run<T>(g, w, o, 1, adj, b, w->x, nt1, o->c_stage * eta * nbred, o->maxit, &its1, &res1, &s1, &e1));
   ETH_CUDA(cudaMemsetAsync(w->x + nt1, 0, (nt - nt1) * 8, g->s));
   // Prop. 2 at the switch (FP64 residual of the full system)
   ETH_TRY(sys_apply(g, 2, false, adj, w->x, G->w));
@@ -751,7 +770,7 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
   st->prop2_lhs = G->gsh->pcg[0];
   st->prop2_bound = std::pow(o->c_stage * eta * nbred, 2) + G->gsh->pcg[1];
   // Step II: full system with M_1
-  ETH_TRY(gmres_run<T>(g, w, o, 2, adj, b, w->x, nt, eta * nb2, o->maxit - its1, &its2, &res2, &s2));
+  ETH_TRY(gmres_run<T>(g, w, o, 2, adj, b, w->x, nt, eta * nb2, o->maxit - its1, &its2, &res2, &s2, &e2));
   ETH_TRY(canonicalize(g, w->x));
   double rr;
   ETH_TRY(true_residual(g, w, b, &rr, adj));
@@ -759,13 +778,14 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
   st->iters_stage2 = its2;
   st->iters_total = its1 + its2;
   st->refine_passes = 0;
+  st->escalations = e1 + e2;
   st->relres_true = std::sqrt(rr) / nb2;
   if (s1 == ETH_ENAN || s2 == ETH_ENAN || !std::isfinite(st->relres_true)) return ETH_ENAN;
   return st->relres_true <= eta * (1.0 + 1e-9) ? ETH_OK : ETH_ENOTCONV;
 }
 
 eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* bsrc) {
-  const int m = std::max(1, std::min(o->restart, GM_MAX));
+  const int m = std::max(1, std::min(std::max(o->restart, o->restart_max), GM_MAX));
   ETH_TRY(gm_alloc(g, w, m));
   // consistent right-hand side (e1 / e0 components removed)
   ETH_CUDA(cudaMemcpyAsync(w->bp, bsrc, (size_t)g->nt * 8, cudaMemcpyDeviceToDevice, g->s));

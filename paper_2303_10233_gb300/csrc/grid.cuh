@@ -62,6 +62,8 @@ struct eth_grid {
   void* ws = nullptr;
   void (*ws_free)(void*) = nullptr;
   long launches = 0;
+  int tile_rows = 0;          // element rows per CTA of the fused K apply (0: default shape)
+  bool tuned = false;         // tile_rows chosen by the autotuner
 };
 
 struct eth_batch {

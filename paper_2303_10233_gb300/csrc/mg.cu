@@ -233,6 +233,8 @@ __global__ void k_q2_coarse_mat(int n, double hx, double hy, double nu, double s
 }
 
 // x(interior) = Ainv * b(interior) per component (blockIdx.y), Q2 lattice.
+// Dense inverses are stored column-major (entry (r, k) at k * m + r), so the
+// threads of a warp (consecutive rows r) read consecutive addresses.
 template <class T>
 __global__ void k_q2_dense_mv(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, const int* done) {
   if (done != nullptr && *done) return;
@@ -244,8 +246,7 @@ __global__ void k_q2_dense_mv(int n, const T* __restrict__ Ainv, const T* __rest
   __syncthreads();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
     T s = 0;
-    const T* row = Ainv + (size_t)r * m;
-    for (int k = 0; k < m; ++k) s += row[k] * sb[k];
+    for (int k = 0; k < m; ++k) s += Ainv[(size_t)k * m + r] * sb[k];
     x[off + (size_t)(r / M + 1) * N + (r % M + 1)] = s;
   }
 }
@@ -312,13 +313,18 @@ __global__ void k_dense_mv(int m, const T* __restrict__ Ainv, const T* __restric
   __syncthreads();
   for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
     T s = 0;
-    const T* row = Ainv + (size_t)r * m;
-    for (int k = 0; k < m; ++k) s += row[k] * sb[k];
+    for (int k = 0; k < m; ++k) s += Ainv[(size_t)k * m + r] * sb[k];
     x[r] = s;
   }
 }
 
 // ---------------------------------------------------------------------------
+// host: in-place transpose of a dense m x m matrix (row-major <-> column-major)
+static void transpose_sq(std::vector<double>& h, int m) {
+  for (int i = 0; i < m; ++i)
+    for (int j = i + 1; j < m; ++j) std::swap(h[(size_t)i * m + j], h[(size_t)j * m + i]);
+}
+
 // host: dense inverse by Gauss-Jordan with partial pivoting (set-up only)
 // ---------------------------------------------------------------------------
 static bool invert(std::vector<double>& A, int m) {
@@ -445,6 +451,7 @@ eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art, bool tran
     for (int i = 0; i < m; ++i)
       for (int j = i + 1; j < m; ++j) std::swap(h[(size_t)i * m + j], h[(size_t)j * m + i]);
   if (!invert(h, m)) { set_error("multigrid: singular coarse operator"); return ETH_EINVAL; }
+  transpose_sq(h, m);   // stored column-major
   ETH_TRY(upload<T>(h, &H.coarse_inv, g->s));
   H.ncoarse = m;
   H.built = true;
@@ -492,6 +499,7 @@ eth_status mg_build_q1(eth_grid* g, Hier<T>& H, int nmin) {
   for (size_t k = 0; k < K.size(); ++k) K[k] += 1.0 / m;
   if (!invert(K, m)) { set_error("multigrid: singular Q1 coarse operator"); return ETH_EINVAL; }
   for (size_t k = 0; k < K.size(); ++k) K[k] -= 1.0 / m;
+  transpose_sq(K, m);   // stored column-major
   ETH_TRY(upload<T>(K, &H.coarse_inv, g->s));
   H.ncoarse = m;
   H.built = true;
@@ -665,11 +673,21 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
     const int l = L.nlev - 1, n = L.n[l], N = 2 * n + 1, M = N - 2, nv = N * N;
     for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * m; t += blockDim.x) {
-      const int c = t / m, r = t - c * m;
-      T acc = 0;
-      for (int k = 0; k < m; ++k) acc += Ainv[(size_t)r * m + k] * B[l][c * nv + (k / M + 1) * N + (k % M + 1)];
-      X[l][c * nv + (r / M + 1) * N + (r % M + 1)] = acc;
+    // both components per row; column-major inverse: coalesced over r, B read as a broadcast
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+      T acc0 = 0, acc1 = 0;
+      const T* col = Ainv + r;
+      for (int ky = 0; ky < M; ++ky) {
+        const T* b0 = B[l] + (ky + 1) * N + 1;
+        for (int kx = 0; kx < M; ++kx, col += m) {
+          const T a = *col;
+          acc0 += a * b0[kx];
+          acc1 += a * b0[kx + nv];
+        }
+      }
+      const int o = (r / M + 1) * N + (r % M + 1);
+      X[l][o] = acc0;
+      X[l][o + nv] = acc1;
     }
     __syncthreads();
   }
@@ -784,7 +802,7 @@ __global__ void __launch_bounds__(1024) k_q1_coarse_vc(CoarseQ1<T> L, const T* _
     const int l = L.nlev - 1;
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
       T acc = 0;
-      for (int k = 0; k < m; ++k) acc += Apinv[(size_t)r * m + k] * B[l][k];
+      for (int k = 0; k < m; ++k) acc += Apinv[(size_t)k * m + r] * B[l][k];
       X[l][r] = acc;
     }
     __syncthreads();

@@ -1,4 +1,7 @@
 // Operator applies of the public ABI (eth_apply) and right-hand-side assembly.
+#include <map>
+#include <mutex>
+#include <tuple>
 #include "ops.cuh"
 
 namespace eth {
@@ -22,15 +25,37 @@ template <>
 const double* wind_ptr<double>(eth_grid* g) { return g->wind; }
 
 // y = K x with the velocity block F (Stokes: nu*A, Oseen: nu*A + N) --------
-template <class CT, int F>
+// TUNED: the fused K apply, launched with the grid's (autotuned) tile: 32 x rows
+// elements, one tile per CTA, or (FP32 element arithmetic only) the persistent
+// pipelined 32 x 8 kernel.  A tile code is rows, or rows + TILE_PERSIST.
+int tile_code(const eth_grid* g) { return g->tile_rows ? g->tile_rows : ETH_TEY; }
+int tile_rows(const eth_grid* g) { return tile_code(g) % TILE_PERSIST; }
+bool tile_persistent(const eth_grid* g) { return tile_code(g) >= TILE_PERSIST; }
+
+template <class CT, int F, bool TUNED = false>
 static eth_status run_q2(eth_grid* g, const double* x, const double* p, double* y, double* yp,
-                         const int* done = nullptr, Slot* slot = nullptr, int slot_off = 0) {
+                         const int* done = nullptr, Slot* slot = nullptr, int slot_off = 0, int code = 0) {
   Q2Params<double, double, CT> P{};
   P.n = g->n; P.hx = (CT)g->hx; P.hy = (CT)g->hy; P.nu = (CT)g->nu;
   P.x = x; P.p = p; P.w = wind_ptr<CT>(g); P.y = y; P.yp = yp;
   P.done = done;
   if (slot) { P.slot = *slot; P.slot_off = slot_off; P.dv = x; P.dvp = p; }
-  ETH_CUDA((launch_q2<double, double, CT, F, EPI_APPLY>(P, g->s)));
+  if (TUNED) {
+    if (!code) code = tile_code(g);
+    const int ty = code % TILE_PERSIST;
+    if constexpr (sizeof(CT) == 4 && (F & QF_XIN) && !(F & (QF_NOBC | QF_MASS))) {
+      if (code >= TILE_PERSIST) {
+        if (slot) P.slot.total = q2p_blocks<F>(g->n);
+        ETH_CUDA((launch_q2p<F>(P, g->s)));
+        g->launches++;
+        return ETH_OK;
+      }
+    }
+    if (slot) P.slot.total = q2_blocks(g->n, ty);
+    ETH_CUDA((launch_q2_ty<double, double, CT, F, EPI_APPLY>(P, g->s, ty)));
+  } else {
+    ETH_CUDA((launch_q2<double, double, CT, F, EPI_APPLY>(P, g->s)));
+  }
   g->launches++;
   return ETH_OK;
 }
@@ -41,8 +66,8 @@ static eth_status apply_t(eth_grid* g, eth_op op, const double* x, double* y) {
   const size_t nu2 = 2 * (size_t)g->nv;
   switch (op) {
     case ETH_OP_K:
-      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
-      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
     case ETH_OP_KT:
       if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
       return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
@@ -86,32 +111,103 @@ eth_status op_apply(eth_grid* g, eth_op op, bool fp32, const double* x, double* 
 
 // K z with the fused FP64 dot <Kz, z> into slot `which` (MINRES delta) ----
 template <class CT>
-static eth_status apply_dot_t(eth_grid* g, bool trans, const double* x, double* y, Slot s, const int* done) {
+static eth_status apply_dot_t(eth_grid* g, bool trans, const double* x, double* y, Slot s, const int* done, int ty) {
   const bool conv = g->kind == ETH_OSEEN;
   const size_t nu2 = 2 * (size_t)g->nv;
-  s.total = q2_blocks(g->n);
   if (conv && trans)
-    return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT>(g, x, x + nu2, y, y + nu2, done, &s);
+    return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT, true>(g, x, x + nu2, y, y + nu2, done, &s, 0, ty);
   if (conv)
-    return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT>(g, x, x + nu2, y, y + nu2, done, &s);
-  return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT>(g, x, x + nu2, y, y + nu2, done, &s);
+    return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT, true>(g, x, x + nu2, y, y + nu2, done, &s, 0, ty);
+  return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT | QF_DOT, true>(g, x, x + nu2, y, y + nu2, done, &s, 0, ty);
 }
 
 eth_status op_apply_K_dot(eth_grid* g, bool fp32, bool trans, const double* x, double* y, Slot s, const int* done) {
-  return fp32 ? apply_dot_t<float>(g, trans, x, y, s, done) : apply_dot_t<double>(g, trans, x, y, s, done);
+  return fp32 ? apply_dot_t<float>(g, trans, x, y, s, done, 0) : apply_dot_t<double>(g, trans, x, y, s, done, 0);
 }
 
 eth_status op_apply_K(eth_grid* g, bool fp32, bool trans, const double* x, double* y, const int* done) {
   const bool conv = g->kind == ETH_OSEEN;
   const size_t nu2 = 2 * (size_t)g->nv;
   if (fp32) {
-    if (conv && trans) return run_q2<float, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
-    if (conv) return run_q2<float, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
-    return run_q2<float, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+    if (conv && trans) return run_q2<float, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2, done);
+    if (conv) return run_q2<float, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2, done);
+    return run_q2<float, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2, done);
   }
   if (conv && trans) return run_q2<double, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
   if (conv) return run_q2<double, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
   return run_q2<double, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+}
+
+// ---------------------------------------------------------------------------
+// Tile-height autotuner: times the fused K apply with its dot (the form the
+// Krylov loops launch) for every tile height whose block count fits the
+// reduction partials, on the grid's right-hand side, and keeps the fastest.
+// Results are cached per (n, operator kind, precision) for the process.
+// ---------------------------------------------------------------------------
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, int> g_tune_cache;
+}  // namespace
+
+eth_status tune_tiles(eth_grid* g, bool fp32) {
+  if (g->tuned) return ETH_OK;
+  const auto key = std::make_tuple(g->n, (int)g->kind, fp32 ? 1 : 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) { g->tile_rows = it->second; g->tuned = true; return ETH_OK; }
+  }
+  cudaEvent_t e0, e1;
+  ETH_CUDA(cudaEventCreate(&e0));
+  ETH_CUDA(cudaEventCreate(&e1));
+  int best = ETH_TEY;
+  float best_ms = 1e30f;
+  eth_status st = ETH_OK;
+  const int cands[4] = {4, 8, 16, 8 + TILE_PERSIST};
+  for (int ty : cands) {
+    if (ty >= TILE_PERSIST && !fp32) continue;
+    if (ty < TILE_PERSIST && q2_blocks(g->n, ty) > g->part_cap) continue;
+    Slot s = make_slot(g, 11, 0);
+    for (int r = 0; r < 2 && st == ETH_OK; ++r) st = op_apply_tiles(g, fp32, g->b, g->tmp, s, ty);
+    if (st != ETH_OK) break;
+    cudaEventRecord(e0, g->s);
+    constexpr int REPS = 6;
+    for (int r = 0; r < REPS && st == ETH_OK; ++r) st = op_apply_tiles(g, fp32, g->b, g->tmp, s, ty);
+    cudaEventRecord(e1, g->s);
+    if (st != ETH_OK) break;
+    if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_status(cudaGetLastError(), "autotune"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = ty; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != ETH_OK) return st;
+  g->tile_rows = best;
+  g->tuned = true;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
+  return ETH_OK;
+}
+
+}  // namespace eth
+
+extern "C" eth_status eth_grid_set_tile(eth_grid* g, int rows, int persistent) {
+  using namespace eth;
+  if (!g) { set_error("eth_grid_set_tile: NULL grid"); return ETH_EINVAL; }
+  if (rows == 0) { g->tile_rows = 0; g->tuned = false; return ETH_OK; }
+  if (!q2_tile_ok(rows)) { set_error("eth_grid_set_tile: rows=%d not in {4, 8, 16}", rows); return ETH_EINVAL; }
+  if (persistent && rows != 8) { set_error("eth_grid_set_tile: the persistent kernel has 8 rows"); return ETH_EINVAL; }
+  if (!persistent && q2_blocks(g->n, rows) > g->part_cap) { set_error("eth_grid_set_tile: too many tiles for n=%d", g->n); return ETH_EINVAL; }
+  g->tile_rows = rows + (persistent ? TILE_PERSIST : 0);
+  g->tuned = true;
+  return ETH_OK;
+}
+
+namespace eth {
+
+eth_status op_apply_tiles(eth_grid* g, bool fp32, const double* x, double* y, Slot s, int ty) {
+  return fp32 ? apply_dot_t<float>(g, false, x, y, s, nullptr, ty) : apply_dot_t<double>(g, false, x, y, s, nullptr, ty);
 }
 
 // ---------------------------------------------------------------------------

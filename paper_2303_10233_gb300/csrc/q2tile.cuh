@@ -99,6 +99,20 @@ __host__ __device__ constexpr double g12(int d, int b) {
 __host__ __device__ constexpr double c0v(int a) { return a == 0 ? -1.0 : (a == 1 ? 0.0 : 1.0); }
 __host__ __device__ constexpr double g0v(int b) { return b == 1 ? 4.0 / 6.0 : 1.0 / 6.0; }
 
+// FP64 -> FP32 of a staged input (warp-collective; masked lanes give 0).
+template <class CT, class TI>
+__device__ __forceinline__ CT cvt_stage(TI v, bool valid) {
+  if constexpr (sizeof(TI) == 8 && sizeof(CT) == 4) {
+#if ETH_IN_FASTCVT
+    return f64_to_f32_warp(v, valid);
+#else
+    return valid ? f64_to_f32_bits(v) : 0.0f;
+#endif
+  } else {
+    return valid ? (CT)v : CT(0);
+  }
+}
+
 // FP32 -> FP64 of kernel outputs: the conversion instruction (FP64 pipe, idle in
 // FP32 element kernels) or the integer bit path (ALU pipe).
 template <class TO, class CT>
@@ -280,8 +294,11 @@ __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9
   }
 }
 
-template <class TI, class TO, class CT, int F, int EPI>
-__global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
+// TY = element rows per CTA (tile 32 x TY computed, 31 x (TY-1) owned); the
+// constants below shadow the default-shape ones of the namespace.
+template <class TI, class TO, class CT, int F, int EPI, int TY = ETH_TEY>
+__global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
+  constexpr int TEY = TY, OEY = TY - 1, Q2T = TEX * TY, SQY = 2 * TY + 1, SPY = TY + 1;
   constexpr bool CONV = F & QF_CONV, XIN = F & QF_XIN, PIN = F & QF_PIN, HP0 = F & QF_P0,
                  UOUT = F & QF_UOUT, POUT = F & QF_POUT, DOT = F & QF_DOT, NOBC = F & QF_NOBC,
                  JB = F & QF_SRC_JB, XPC = F & QF_SRC_XPC;
@@ -306,16 +323,18 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
     constexpr int NLD = (SQY * SQX + Q2T - 1) / Q2T;
     TI v0[NLD], v1[NLD];
     CT w0[NLD], w1[NLD];
+    bool ok[NLD];
 #pragma unroll
     for (int r = 0; r < NLD; ++r) {
       const int k = tid + r * Q2T;
       const int lj = k / SQX, li = k - lj * SQX;
       const int i = gi0 + li, j = gj0 + lj;
-      v0[r] = 0; v1[r] = 0; w0[r] = 0; w1[r] = 0;
+      v0[r] = 0; v1[r] = 0; w0[r] = 0; w1[r] = 0; ok[r] = false;
       if (k < SQY * SQX && i >= 0 && i < N && j >= 0 && j < N) {
         const size_t g = (size_t)j * N + i;
         const bool bnd = !NOBC && (i == 0 || j == 0 || i == N - 1 || j == N - 1);
         if (XIN && !bnd) {
+          ok[r] = true;
           if (JB) { v0[r] = P.bx[g]; v1[r] = P.bx[g + nv]; w0[r] = P.dinv[g]; }
           else { v0[r] = P.x[g]; v1[r] = P.x[g + nv]; }
         }
@@ -325,11 +344,14 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
 #pragma unroll
     for (int r = 0; r < NLD; ++r) {
       const int k = tid + r * Q2T;
+      // every lane converts (warp-collective); masked lanes give 0
+      const CT c0 = XIN ? cvt_stage<CT, TI>(v0[r], ok[r]) : CT(0);
+      const CT c1 = XIN ? cvt_stage<CT, TI>(v1[r], ok[r]) : CT(0);
       if (k < SQY * SQX) {
         if (JB) {
           const CT om = P.omega * w0[r];
-          sx[k] = om * cvt<CT, TI>(v0[r]); sx[SQY * SQX + k] = om * cvt<CT, TI>(v1[r]);
-        } else if (XIN) { sx[k] = cvt<CT, TI>(v0[r]); sx[SQY * SQX + k] = cvt<CT, TI>(v1[r]); }
+          sx[k] = om * c0; sx[SQY * SQX + k] = om * c1;
+        } else if (XIN) { sx[k] = c0; sx[SQY * SQX + k] = c1; }
         if (CONV && !JB) { sw[k] = w0[r]; sw[SQY * SQX + k] = w1[r]; }
       }
     }
@@ -554,26 +576,40 @@ __global__ void __launch_bounds__(Q2T) k_q2(Q2Params<TI, TO, CT> P) {
   }
 }
 
-inline size_t q2_smem_bytes(int F, size_t ct_size) {
+inline size_t q2_smem_bytes(int F, size_t ct_size, int ty = ETH_TEY) {
   const bool conv = F & QF_CONV;
-  size_t nct = 2 * SQY * SQX + (conv ? 2 * SQY * SQX : 0) + SPY * SPX + TEY * TEX + NEO * Q2T;
+  const size_t sqy = 2 * ty + 1, spy = ty + 1, q2t = (size_t)TEX * ty;
+  size_t nct = 2 * sqy * SQX + (conv ? 2 * sqy * SQX : 0) + spy * SPX + q2t + NEO * q2t;
   return nct * ct_size;
 }
 
-inline dim3 q2_grid(int n) { return dim3(cdiv(n, OEX), cdiv(n, OEY)); }
-inline int q2_blocks(int n) { return (int)(cdiv(n, OEX) * cdiv(n, OEY)); }
+inline dim3 q2_grid(int n, int ty = ETH_TEY) { return dim3(cdiv(n, OEX), cdiv(n, ty - 1)); }
+inline int q2_blocks(int n, int ty = ETH_TEY) { return (int)(cdiv(n, OEX) * cdiv(n, ty - 1)); }
 
-template <class TI, class TO, class CT, int F, int EPI>
+template <class TI, class TO, class CT, int F, int EPI, int TY = ETH_TEY>
 cudaError_t launch_q2(const Q2Params<TI, TO, CT>& P, cudaStream_t s) {
   static bool attr_set = false;
-  const size_t smem = q2_smem_bytes(F, sizeof(CT));
+  const size_t smem = q2_smem_bytes(F, sizeof(CT), TY);
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_q2<TI, TO, CT, F, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_q2<TI, TO, CT, F, EPI, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  k_q2<TI, TO, CT, F, EPI><<<q2_grid(P.n), Q2T, smem, s>>>(P);
+  k_q2<TI, TO, CT, F, EPI, TY><<<q2_grid(P.n, TY), TEX * TY, smem, s>>>(P);
   return cudaGetLastError();
+}
+
+// Tile heights a grid may select (the autotuned K apply); others use ETH_TEY.
+constexpr int Q2_TILE_ROWS[3] = {4, 8, 16};
+inline bool q2_tile_ok(int ty) { return ty == 4 || ty == 8 || ty == 16; }
+
+template <class TI, class TO, class CT, int F, int EPI>
+cudaError_t launch_q2_ty(const Q2Params<TI, TO, CT>& P, cudaStream_t s, int ty) {
+  switch (ty) {
+    case 4: return launch_q2<TI, TO, CT, F, EPI, 4>(P, s);
+    case 16: return launch_q2<TI, TO, CT, F, EPI, 16>(P, s);
+    default: return launch_q2<TI, TO, CT, F, EPI, 8>(P, s);
+  }
 }
 
 }  // namespace eth

@@ -648,7 +648,7 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
   int j = 1;
   const bool use_graph = o->graph != 0;
   const int key = (int)fp32 * 1000 + (int)(sizeof(T)) * 10 + o->mg_pre + 100 * o->mg_post + 10000 * o->a_exact +
-                  20000 * o->mq_mode;
+                  20000 * o->mq_mode + 100000 * tile_code(g);
   while (true) {
     if (use_graph) {
       if (!w->gexec || w->gkey != key) {
@@ -691,7 +691,7 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
 
 template <class T>
 eth_status ensure_hier(eth_grid* g, Work* w, const eth_opts* o) {
-  const int nmin = std::max(2, o->mg_min_n);
+  const int nmin = o->mg_min_n > 0 ? std::max(2, o->mg_min_n) : (g->kind == ETH_OSEEN ? 8 : 4);
   if (w->nmin_built != nmin) {
     mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd); mg_free(w->vft); mg_free(w->vdt);
     if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; w->gkey = -1; }
@@ -824,6 +824,7 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   StreamSwap guard(g, w);
   if (o.precision == ETH_MIXED) ETH_TRY(ensure_hier<float>(g, w, &o)); else ETH_TRY(ensure_hier<double>(g, w, &o));
   if (o.a_exact || o.mq_mode == ETH_MQ_EXACT) ETH_TRY(ensure_pcg(g, w));
+  if (o.autotune) ETH_TRY(tune_tiles(g, o.precision == ETH_MIXED));
   const long l0 = g->launches;
   ETH_CUDA(cudaEventRecord(w->t0, g->s));
   const size_t nu2 = 2 * (size_t)g->nv;
@@ -845,6 +846,8 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   st.seconds = ms * 1e-3;
   st.status = r;
   st.kernel_launches = (int)(g->launches - l0);
+  st.tile_rows = tile_rows(g);
+  st.tile_persistent = tile_persistent(g) && o.precision == ETH_MIXED;
   if (stats) *stats = st;
   return r;
 }
@@ -885,6 +888,7 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
   StreamSwap guard(g, w);
   w->need_adj = true;
   if (o.precision == ETH_MIXED) ETH_TRY(ensure_hier<float>(g, w, &o)); else ETH_TRY(ensure_hier<double>(g, w, &o));
+  if (o.autotune) ETH_TRY(tune_tiles(g, o.precision == ETH_MIXED));
   const long l0 = g->launches;
   ETH_CUDA(cudaEventRecord(w->t0, g->s));
   const size_t nu2 = 2 * (size_t)g->nv, np = (size_t)g->n1 + g->n0;
@@ -908,6 +912,8 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
   st.seconds = ms * 1e-3;
   st.status = r;
   st.kernel_launches = (int)(g->launches - l0);
+  st.tile_rows = tile_rows(g);
+  st.tile_persistent = tile_persistent(g) && o.precision == ETH_MIXED;
   if (stats) *stats = st;
   return r;
 }
@@ -949,6 +955,11 @@ eth_status eth_batch_solve(eth_batch* b, const eth_opts* opts, double* const* u,
   const int nw = std::max(1, std::min(count, b->workers > 0 ? b->workers : 16));
   int dev = 0;
   cudaGetDevice(&dev);
+  // the autotuner times kernels: run it for every instance before the workers overlap them
+  eth_opts o;
+  if (opts) o = *opts; else eth_default_opts(&o);
+  if (o.autotune)
+    for (int i : order) ETH_TRY(tune_tiles(b->grids[i], o.precision == ETH_MIXED));
   auto worker = [&]() {
     cudaSetDevice(dev);
     while (true) {

@@ -34,7 +34,8 @@ class Opts(ctypes.Structure):
                 ("c_stage", ctypes.c_double), ("precision", ctypes.c_int), ("mg_pre", ctypes.c_int),
                 ("mg_post", ctypes.c_int), ("mg_min_n", ctypes.c_int), ("mq_mode", ctypes.c_int),
                 ("a_exact", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("refine_inner_tol", ctypes.c_double), ("graph", ctypes.c_int), ("verbose", ctypes.c_int)]
+                ("refine_inner_tol", ctypes.c_double), ("graph", ctypes.c_int), ("verbose", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("restart_max", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -43,7 +44,9 @@ class Stats(ctypes.Structure):
                 ("relres_true", ctypes.c_double), ("relres0", ctypes.c_double),
                 ("prop2_lhs", ctypes.c_double), ("prop2_bound", ctypes.c_double),
                 ("seconds", ctypes.c_double), ("alg_bytes", ctypes.c_double),
-                ("status", ctypes.c_int), ("kernel_launches", ctypes.c_int)]
+                ("status", ctypes.c_int), ("kernel_launches", ctypes.c_int),
+                ("escalations", ctypes.c_int), ("tile_rows", ctypes.c_int),
+                ("tile_persistent", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,6 +72,7 @@ def load(path=LIB_PATH):
         "eth_default_opts": (None, [ctypes.POINTER(Opts)]),
         "eth_grid_create": (i, [i, d, d, d, d, i, vp, ctypes.POINTER(vp)]),
         "eth_grid_destroy": (None, [vp]),
+        "eth_grid_set_tile": (i, [vp, i, i]),
         "eth_set_coefficients": (i, [vp, d, vp]),
         "eth_set_rhs": (i, [vp, vp, vp]),
         "eth_get_rhs": (i, [vp, vp]),
@@ -163,6 +167,11 @@ class Grid:
     def set_coefficients(self, nu, wind=None):
         self._wind = wind
         _check(load().eth_set_coefficients(self.h, float(nu), _ptr(wind)))
+
+    def set_tile(self, rows, persistent=False):
+        """Pins the fused K apply's tile (32 x rows elements, rows in {4, 8, 16}; persistent form with
+        rows = 8); rows = 0 re-enables tuning."""
+        _check(load().eth_grid_set_tile(self.h, int(rows), int(bool(persistent))))
 
     def set_rhs(self, f_nodal, ubc):
         _check(load().eth_set_rhs(self.h, _ptr(f_nodal), _ptr(ubc)))
