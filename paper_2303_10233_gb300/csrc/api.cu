@@ -22,6 +22,7 @@ eth_status cuda_status(cudaError_t e, const char* what) {
 }
 
 __global__ void k_f64_to_f32(size_t m, const double* __restrict__ a, float* __restrict__ b) {
+  ETH_GRID_DEP_WAIT();
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) b[k] = (float)a[k];
 }
 
@@ -91,7 +92,8 @@ eth_status eth_grid_create(int n, double x0, double x1, double y0, double y1, et
   g->s = (cudaStream_t)cuda_stream;
   g->nt = eth_sizes(n, &g->nv, &g->n1, &g->n0);
   const size_t nt = g->nt, nu2 = 2 * (size_t)g->nv;
-  g->part_cap = 1 << 16;
+  // reduction partials per slot: one per CTA of the largest launch (the 32 x 4 tile grid)
+  g->part_cap = std::max(1 << 16, q2_blocks(n, 4));
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
   A((void**)&g->b, nt * 8);

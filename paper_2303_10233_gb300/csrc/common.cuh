@@ -13,6 +13,13 @@
 #include <string>
 #include "eth.h"
 
+// Every kernel starts by waiting for the grids it depends on (griddepcontrol.wait).
+// Outside a programmatic dependency this returns at once; inside the captured
+// solver graphs the kernel-to-kernel edges are programmatic (the downstream
+// grid is launched once all blocks of the upstream grid have started), so the
+// wait is what orders a kernel after its producer and makes its writes visible.
+#define ETH_GRID_DEP_WAIT() asm volatile("griddepcontrol.wait;\n" ::: "memory")
+
 namespace eth {
 
 constexpr double GOFF = 0.38729833462074168852;   // sqrt(3/5)/2

@@ -15,6 +15,8 @@
 // GMRES cycle the operator is applied with FP32 element arithmetic; every
 // restart recomputes the residual with FP64 element arithmetic, which makes
 // the restarts an FP64 iterative refinement.
+#include <map>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include "solve.cuh"
@@ -51,6 +53,8 @@ struct GMRESWork {
   float* q1df = nullptr; double* q1dd = nullptr;   // inverse Q1-mass diagonal
   void* pv[8] = {};                                // Q1 / velocity scratch (type T)
   int pcd_prec = -1;
+  int grp = 16;        // basis vectors per pass of the Gram-Schmidt dot kernel (autotuned)
+  bool grp_tuned = false;
 };
 
 void gmres_free(Work* w) {
@@ -68,7 +72,7 @@ void gmres_free(Work* w) {
 // ---------------------------------------------------------------------------
 // multi-vector kernels: h_i = <V_i, w> (i < nvec) and w -= sum_i h_i V_i
 // ---------------------------------------------------------------------------
-constexpr int MG_GRP = 16;
+constexpr int MG_GRP_MAX = 16;
 
 // last-block sum of partials part[i*nb + b] into out[i]
 __device__ __forceinline__ bool multi_finish(int nvec, int nb, double* part, unsigned* ticket, double* out) {
@@ -89,9 +93,12 @@ __device__ __forceinline__ bool multi_finish(int nvec, int nb, double* part, uns
   return true;
 }
 
-// h_i = <V_i, w> for i < nvec; with wnorm, also out[nvec] = <w, w> (grouped MG_GRP vectors per pass)
+// h_i = <V_i, w> for i < nvec; with wnorm, also out[nvec] = <w, w> (grouped MG_GRP vectors per
+// pass over w: more vectors per pass read w fewer times but hold more accumulators)
+template <int MG_GRP>
 __global__ void k_mdot(size_t n, const double* __restrict__ V, size_t ld, int nvec, const double* __restrict__ w,
                        double* part, unsigned* ticket, double* out, const int* done, const int* skip, int wnorm) {
+  ETH_GRID_DEP_WAIT();
   if ((done && *done) || (skip && *skip)) return;
   const int nb = gridDim.x;
   const int nout = nvec + (wnorm ? 1 : 0);
@@ -145,6 +152,7 @@ __device__ __forceinline__ void arnoldi_finish(GScalars* gs, int j, double wn2) 
 __global__ void k_mupd(size_t n, const double* __restrict__ V, size_t ld, int nvec, const double* __restrict__ h,
                        double* __restrict__ w, int norm, double* part, unsigned* ticket, GScalars* gs, int j, const int* done,
                        const int* skip) {
+  ETH_GRID_DEP_WAIT();
   if ((done && *done) || (skip && *skip)) return;
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
@@ -176,6 +184,7 @@ __global__ void k_mupd(size_t n, const double* __restrict__ V, size_t ld, int nv
 }
 
 __global__ void k_vscale(size_t n, const double* __restrict__ w, double* __restrict__ v, const GScalars* gs, int use_beta) {
+  ETH_GRID_DEP_WAIT();
   if (gs->done && !use_beta) return;
   const double s = 1.0 / (use_beta ? gs->beta : gs->wnorm);
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) v[k] = s * w[k];
@@ -184,6 +193,7 @@ __global__ void k_vscale(size_t n, const double* __restrict__ w, double* __restr
 // r = b - y, ||r||^2 -> gs->beta (sqrt), cycle initialisation of the Givens state
 __global__ void k_gm_resid(size_t n, const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r,
                            double* part, unsigned* ticket, GScalars* gs, double tol_abs) {
+  ETH_GRID_DEP_WAIT();
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     const double v = b[k] - y[k];
@@ -210,6 +220,7 @@ __global__ void k_gm_resid(size_t n, const double* __restrict__ b, const double*
 
 // y = H(0:k,0:k)^{-1} g(0:k) by back substitution (one thread)
 __global__ void k_gm_solve(GScalars* gs) {
+  ETH_GRID_DEP_WAIT();
   const int k = gs->k;
   for (int i = k - 1; i >= 0; --i) {
     double s = gs->g[i];
@@ -220,6 +231,7 @@ __global__ void k_gm_solve(GScalars* gs) {
 
 // x += sum_{i<k} y_i Z_i  (k read on the device)
 __global__ void k_zupd(size_t n, const double* __restrict__ Z, size_t ld, const GScalars* gs, double* __restrict__ x) {
+  ETH_GRID_DEP_WAIT();
   const int kk = gs->k;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     double v = x[k];
@@ -234,6 +246,7 @@ __global__ void k_zupd(size_t n, const double* __restrict__ Z, size_t ld, const 
 // Q1 convection element matrices C_T[a][b] = int_T psi_a (w_h . grad psi_b) (3x3 Gauss, Q2 wind)
 template <class T>
 __global__ void k_q1_conv_mats(int n, double hx, double hy, const double* __restrict__ w, T* __restrict__ C, int trans) {
+  ETH_GRID_DEP_WAIT();
   const int N = 2 * n + 1;
   const size_t nv = (size_t)N * N;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -268,6 +281,7 @@ __global__ void k_q1_conv_mats(int n, double hx, double hy, const double* __rest
 // inverse of the diagonal of the velocity mass matrix (interior nodes), 0 on the boundary
 template <class T>
 __global__ void k_q2_mass_diag(int n, double hx, double hy, T* __restrict__ md) {
+  ETH_GRID_DEP_WAIT();
   const int N = 2 * n + 1;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N * N; node += gridDim.x * blockDim.x) {
     const int j = node / N, i = node - j * N;
@@ -281,6 +295,7 @@ __global__ void k_q2_mass_diag(int n, double hx, double hy, T* __restrict__ md) 
 
 template <class T>
 __global__ void k_q1_mass_diag(int n, double hx, double hy, T* __restrict__ d) {
+  ETH_GRID_DEP_WAIT();
   const int M = n + 1;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < M * M; node += gridDim.x * blockDim.x) {
     const int J = node / M, I = node - J * M;
@@ -293,6 +308,7 @@ __global__ void k_q1_mass_diag(int n, double hx, double hy, T* __restrict__ d) {
 template <class T>
 __global__ void k_cheb_step(int n, T area, const T* __restrict__ d_in, T* __restrict__ r, T* __restrict__ x, T* __restrict__ dn,
                             const T* __restrict__ dinv, T c1, T c2, const int* done) {
+  ETH_GRID_DEP_WAIT();
   const T* d = d_in;
   if (done && *done) return;
   const int M = n + 1;
@@ -316,6 +332,7 @@ __global__ void k_cheb_step(int n, T area, const T* __restrict__ d_in, T* __rest
 template <class TI, class T>
 __global__ void k_cheb_init(int m, T theta, const TI* __restrict__ b, const T* __restrict__ dinv, T* __restrict__ r,
                             T* __restrict__ x, T* __restrict__ d, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done && *done) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
     const T v = (T)b[k];
@@ -328,6 +345,7 @@ __global__ void k_cheb_init(int m, T theta, const TI* __restrict__ b, const T* _
 // generic small vector kernels on type T (Q1 lattice)
 template <class T>
 __global__ void k_axpy_t(int m, T a, const T* __restrict__ x, T* __restrict__ y) {
+  ETH_GRID_DEP_WAIT();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) y[k] += a * x[k];
 }
 
@@ -335,6 +353,7 @@ __global__ void k_axpy_t(int m, T a, const T* __restrict__ x, T* __restrict__ y)
 template <class T>
 __global__ void k_pcg_dot(int m, const T* __restrict__ a, const T* __restrict__ b, double* part, unsigned* ticket, double* out,
                           const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done && *done) return;
   double acc = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) acc += (double)a[k] * (double)b[k];
@@ -348,6 +367,7 @@ __global__ void k_pcg_dot(int m, const T* __restrict__ a, const T* __restrict__ 
 template <class T>
 __global__ void k_pcg_xr(int m, const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
                          const GScalars* gs, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done && *done) return;
   const double pap = gs->pcg[1];
   const T a = (T)(pap != 0.0 ? gs->pcg[0] / pap : 0.0);   // zero right-hand side: stay at zero
@@ -360,27 +380,32 @@ __global__ void k_pcg_xr(int m, const T* __restrict__ p, const T* __restrict__ q
 // p = z + (rz_new / rz) p ; rz = rz_new
 template <class T>
 __global__ void k_pcg_p(int m, const T* __restrict__ z, T* __restrict__ p, GScalars* gs, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done && *done) return;
   const T bt = (T)(gs->pcg[0] != 0.0 ? gs->pcg[2] / gs->pcg[0] : 0.0);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) p[k] = z[k] + bt * p[k];
   __syncthreads();
 }
-__global__ void k_pcg_shift(GScalars* gs) { gs->pcg[0] = gs->pcg[2]; }
+__global__ void k_pcg_shift(GScalars* gs) {
+  ETH_GRID_DEP_WAIT(); gs->pcg[0] = gs->pcg[2]; }
 
 template <class T>
 __global__ void k_copy_t(int m, const T* __restrict__ a, T* __restrict__ b) {
+  ETH_GRID_DEP_WAIT();
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) b[k] = a[k];
 }
 
 // z_p = -(x - mean x) written as FP64 (mean from gs->pcg[3])
 template <class T>
 __global__ void k_pcd_out(int m, const T* __restrict__ x, double* __restrict__ zp, const GScalars* gs, double scale) {
+  ETH_GRID_DEP_WAIT();
   const double mean = gs->pcg[3] / m;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) zp[k] = scale * ((double)x[k] - mean);
 }
 
 template <class T>
 __global__ void k_sum_t(int m, const T* __restrict__ a, double* part, unsigned* ticket, double* out) {
+  ETH_GRID_DEP_WAIT();
   double acc = 0.0;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) acc += (double)a[k];
   double v[1] = {acc};
@@ -391,11 +416,13 @@ __global__ void k_sum_t(int m, const T* __restrict__ a, double* part, unsigned* 
 
 template <class T>
 __global__ void k_sub_mean_t(int m, T* __restrict__ a, const double* sum) {
+  ETH_GRID_DEP_WAIT();
   const T mu = (T)(*sum / m);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) a[k] -= mu;
 }
 
 __global__ void k_oseen_scalars(Scalars* sc, double n1, double n0, double mqc, double nuq) {
+  ETH_GRID_DEP_WAIT();
   sc->v[S_NP1] = n1; sc->v[S_NP0] = n0; sc->v[S_MQC] = mqc; sc->v[S_MQNU] = nuq;
   sc->done = 0;
 }
@@ -404,6 +431,56 @@ __global__ void k_oseen_scalars(Scalars* sc, double n1, double n0, double mqc, d
 // host side
 // ---------------------------------------------------------------------------
 static int gb(size_t m) { return vblocks(m); }
+
+static eth_status launch_mdot(GMRESWork* G, int nb, cudaStream_t s, size_t ntv, size_t ld, int nvec, double* out,
+                              const int* done, const int* skip, int wnorm) {
+  switch (G->grp) {
+    case 4: k_mdot<4><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm); break;
+    case 8: k_mdot<8><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm); break;
+    default: k_mdot<16><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm); break;
+  }
+  ETH_CUDA(cudaGetLastError());
+  return ETH_OK;
+}
+
+// Autotuner of the Gram-Schmidt dot kernel: times the vectors-per-pass choices
+// {4, 8, 16} on a 32-vector dot against the basis storage (its contents do not
+// matter for the timing) and keeps the fastest; cached per vector length.
+static eth_status tune_cgs(eth_grid* g, GMRESWork* G) {
+  static std::mutex mu;
+  static std::map<size_t, int> cache;
+  const size_t ntv = g->nt;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(ntv);
+    if (it != cache.end()) { G->grp = it->second; G->grp_tuned = true; return ETH_OK; }
+  }
+  const int nvec = std::min(G->m, 32);
+  const int nb = gb(ntv);
+  cudaEvent_t e0, e1;
+  ETH_CUDA(cudaEventCreate(&e0));
+  ETH_CUDA(cudaEventCreate(&e1));
+  int best = 16;
+  float best_ms = 1e30f;
+  for (int grp : {4, 8, 16}) {
+    G->grp = grp;
+    ETH_TRY(launch_mdot(G, nb, g->s, ntv, G->cap, nvec, &G->gs->h1[0], nullptr, nullptr, 1));
+    cudaEventRecord(e0, g->s);
+    for (int r = 0; r < 3; ++r) ETH_TRY(launch_mdot(G, nb, g->s, ntv, G->cap, nvec, &G->gs->h1[0], nullptr, nullptr, 1));
+    cudaEventRecord(e1, g->s);
+    ETH_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best_ms) { best_ms = ms; best = grp; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  G->grp = best;
+  G->grp_tuned = true;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[ntv] = best;
+  return ETH_OK;
+}
 
 static eth_status gm_alloc(eth_grid* g, Work* w, int m) {
   GMRESWork* G = w->gm;
@@ -497,6 +574,7 @@ static eth_status ap_apply(eth_grid* g, GMRESWork* G, const T* p, T* q, const in
 template <class T>
 __global__ void k_q1_j0(int m, T omega, const T* __restrict__ dinv, const T* __restrict__ r, T* __restrict__ b,
                         T* __restrict__ x, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done && *done) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
     const T v = r[k];
@@ -698,9 +776,9 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
       double* h2 = &G->gs->h2[0];
       // classical Gram-Schmidt with selective reorthogonalisation (DGKS, 0.7)
       const int* sk = &G->gs->skip2;
-      k_mdot<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, G->w, G->part, G->ticket + 3, h1, done, nullptr, 1);
+      ETH_TRY(launch_mdot(G, nb, g->s, ntv, ld, j + 1, h1, done, nullptr, 1));
       k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h1, G->w, 2, G->part, G->ticket + 4, G->gs, j, done, nullptr);
-      k_mdot<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, G->w, G->part, G->ticket + 3, h2, done, sk, 0);
+      ETH_TRY(launch_mdot(G, nb, g->s, ntv, ld, j + 1, h2, done, sk, 0));
       k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h2, G->w, 1, G->part, G->ticket + 4, G->gs, j, done, sk);
       k_vscale<<<nb, 256, 0, g->s>>>(ntv, G->w, G->V + (size_t)(j + 1) * ld, G->gs, 0);
       ETH_CUDA(cudaGetLastError());
@@ -724,11 +802,13 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
 }
 
 __global__ void k_copy_d(size_t m, const double* __restrict__ a, double* __restrict__ b) {
+  ETH_GRID_DEP_WAIT();
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) b[k] = a[k];
 }
 
 // Prop. 2 quantities at the stage switch: ||z*||^2 and ||r0*||^2 (P0 block)
 __global__ void k_prop2(size_t nt, size_t off0, const double* __restrict__ r, double* part, unsigned* ticket, double* out) {
+  ETH_GRID_DEP_WAIT();
   double a = 0.0, c = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
     const double v = r[k] * r[k];
@@ -787,6 +867,7 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
 eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* bsrc) {
   const int m = std::max(1, std::min(std::max(o->restart, o->restart_max), GM_MAX));
   ETH_TRY(gm_alloc(g, w, m));
+  if (o->autotune && !w->gm->grp_tuned) ETH_TRY(tune_cgs(g, w->gm));
   // consistent right-hand side (e1 / e0 components removed)
   ETH_CUDA(cudaMemcpyAsync(w->bp, bsrc, (size_t)g->nt * 8, cudaMemcpyDeviceToDevice, g->s));
   ETH_TRY(canonicalize(g, w->bp));

@@ -39,6 +39,7 @@ __device__ __forceinline__ double sd_delta(int N, size_t nv, int ex, int ey, con
 
 template <class T>
 __global__ void k_q2_diag(int n, double hx, double hy, double nu, double sdc, const T* __restrict__ w, T* __restrict__ dinv) {
+  ETH_GRID_DEP_WAIT();
   const int N = 2 * n + 1;
   const size_t nv = (size_t)N * N;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < N * N; node += gridDim.x * blockDim.x) {
@@ -73,6 +74,7 @@ __global__ void k_q2_diag(int n, double hx, double hy, double nu, double sdc, co
 template <class TI, class T>
 __global__ void k_q2_jacobi0(int n, T omega, const T* __restrict__ dinv, const TI* __restrict__ bin, T* __restrict__ bc,
                              T* __restrict__ x, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int N = 2 * n + 1;
   const size_t nv = (size_t)N * N;
@@ -106,6 +108,7 @@ __device__ __forceinline__ int q2_pw(int i, float& w0, float& w1, float& w2) {
 
 template <class T>
 __global__ void k_q2_restrict(int nc, const T* __restrict__ rf, T* __restrict__ bc, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int Nc = 2 * nc + 1, Nf = 4 * nc + 1;
   const size_t nvc = (size_t)Nc * Nc, nvf = (size_t)Nf * Nf;
@@ -138,6 +141,7 @@ __global__ void k_q2_restrict(int nc, const T* __restrict__ rf, T* __restrict__ 
 
 template <class T>
 __global__ void k_q2_prolong_add(int nc, const T* __restrict__ xc, T* __restrict__ xf, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int Nc = 2 * nc + 1, Nf = 4 * nc + 1;
   const size_t nvc = (size_t)Nc * Nc, nvf = (size_t)Nf * Nf;
@@ -164,6 +168,7 @@ __global__ void k_q2_prolong_add(int nc, const T* __restrict__ xc, T* __restrict
 
 template <class T>
 __global__ void k_q2_inject(int nc, const T* __restrict__ wf, T* __restrict__ wc) {
+  ETH_GRID_DEP_WAIT();
   const int Nc = 2 * nc + 1, Nf = 4 * nc + 1;
   const size_t nvc = (size_t)Nc * Nc, nvf = (size_t)Nf * Nf;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Nc * Nc; node += gridDim.x * blockDim.x) {
@@ -176,15 +181,18 @@ __global__ void k_q2_inject(int nc, const T* __restrict__ wf, T* __restrict__ wc
 
 template <class TI>
 __global__ void k_f64_from(size_t m, const TI* __restrict__ a, double* __restrict__ b) {
+  ETH_GRID_DEP_WAIT();
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) b[k] = (double)a[k];
 }
 template <class TO>
 __global__ void k_cast_from_f64(size_t m, const double* __restrict__ a, TO* __restrict__ b) {
+  ETH_GRID_DEP_WAIT();
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) b[k] = (TO)a[k];
 }
 
 // Dense matrix of the interior scalar operator on the coarsest grid (FP64 atomics, set-up only).
 __global__ void k_q2_coarse_mat(int n, double hx, double hy, double nu, double sdc, const double* __restrict__ w, double* __restrict__ D) {
+  ETH_GRID_DEP_WAIT();
   const int N = 2 * n + 1, m = (N - 2) * (N - 2);
   const size_t nv = (size_t)N * N;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -237,6 +245,7 @@ __global__ void k_q2_coarse_mat(int n, double hx, double hy, double nu, double s
 // threads of a warp (consecutive rows r) read consecutive addresses.
 template <class T>
 __global__ void k_q2_dense_mv(int n, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char sm[];
   T* sb = reinterpret_cast<T*>(sm);
@@ -256,6 +265,7 @@ __global__ void k_q2_dense_mv(int n, const T* __restrict__ Ainv, const T* __rest
 // ---------------------------------------------------------------------------
 template <class T>
 __global__ void k_q1_diag_lap(int n, double hx, double hy, T* __restrict__ dinv) {
+  ETH_GRID_DEP_WAIT();
   const int M = n + 1;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < M * M; node += gridDim.x * blockDim.x) {
     const int J = node / M, I = node - J * M;
@@ -266,6 +276,7 @@ __global__ void k_q1_diag_lap(int n, double hx, double hy, T* __restrict__ dinv)
 
 template <class T>
 __global__ void k_q1_restrict(int nc, const T* __restrict__ rf, T* __restrict__ bc, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int Mc = nc + 1, Mf = 2 * nc + 1;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Mc * Mc; node += gridDim.x * blockDim.x) {
@@ -287,6 +298,7 @@ __global__ void k_q1_restrict(int nc, const T* __restrict__ rf, T* __restrict__ 
 
 template <class T>
 __global__ void k_q1_prolong_add(int nc, const T* __restrict__ xc, T* __restrict__ xf, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int Mc = nc + 1, Mf = 2 * nc + 1;
   for (int node = blockIdx.x * blockDim.x + threadIdx.x; node < Mf * Mf; node += gridDim.x * blockDim.x) {
@@ -299,6 +311,7 @@ __global__ void k_q1_prolong_add(int nc, const T* __restrict__ xc, T* __restrict
 
 template <class T>
 __global__ void k_q1_jacobi0(int n, T omega, const T* __restrict__ dinv, const T* __restrict__ b, T* __restrict__ x, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int tot = (n + 1) * (n + 1);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < tot; k += gridDim.x * blockDim.x) x[k] = omega * dinv[k] * b[k];
@@ -306,6 +319,7 @@ __global__ void k_q1_jacobi0(int n, T omega, const T* __restrict__ dinv, const T
 
 template <class T>
 __global__ void k_dense_mv(int m, const T* __restrict__ Ainv, const T* __restrict__ b, T* __restrict__ x, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char sm[];
   T* sb = reinterpret_cast<T*>(sm);
@@ -600,19 +614,34 @@ __device__ void cq2_residual_node(int n, T hx, T hy, T nu, const T* KM, const T*
 template <class T, int FL>
 __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __restrict__ Ainv, int m,
                                                         const T* __restrict__ bin, T* __restrict__ xout, T omega,
-                                                        int pre, int post, const int* done) {
+                                                        int pre, int post, const int* done, int ainv_smem) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  T *X[CMAXL], *B[CMAXL], *R[CMAXL];
+  constexpr bool CONVL = FL & QF_CONV;
+  // per level: X, B, R (2 N^2 each), the inverse diagonal (N^2) and the wind (2 N^2) staged
+  // from global memory once, so the sweeps below touch shared memory only
+  T *X[CMAXL], *B[CMAXL], *R[CMAXL], *D[CMAXL], *Wl[CMAXL];
   size_t off = 0;
   for (int l = 0; l < L.nlev; ++l) {
     const int N = 2 * L.n[l] + 1;
     X[l] = sm + off; off += 2 * N * N;
     B[l] = sm + off; off += 2 * N * N;
     R[l] = sm + off; off += 2 * N * N;
+    D[l] = sm + off; off += N * N;
+    Wl[l] = sm + off; off += CONVL ? 2 * N * N : 0;
+    for (int k = threadIdx.x; k < N * N; k += blockDim.x) D[l][k] = L.dinv[l][k];
+    if (CONVL)
+      for (int k = threadIdx.x; k < 2 * N * N; k += blockDim.x) Wl[l][k] = L.w[l][k];
   }
-  constexpr bool NODE = !(FL & QF_CONV);
+  const T* Ai = Ainv;   // dense coarse inverse: staged too when it fits (ainv_smem)
+  if (ainv_smem) {
+    T* sa = sm + off;
+    for (int k = threadIdx.x; k < m * m; k += blockDim.x) sa[k] = Ainv[k];
+    Ai = sa;
+  }
+  constexpr bool NODE = !CONVL;
   __shared__ T KM[81], MK[81];
   if (NODE) {
     for (int k = threadIdx.x; k < 81; k += blockDim.x) {
@@ -623,7 +652,7 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
   }
   auto resid = [&](int l) {
     if (NODE) cq2_residual_node<T>(L.n[l], L.hx[l], L.hy[l], L.nu[l], KM, MK, X[l], B[l], R[l]);
-    else cq2_residual<T, FL>(L.n[l], L.hx[l], L.hy[l], L.nu[l], L.sd[l], L.w[l], X[l], B[l], R[l]);
+    else cq2_residual<T, FL>(L.n[l], L.hx[l], L.hy[l], L.nu[l], L.sd[l], Wl[l], X[l], B[l], R[l]);
   };
   {
     const int N = 2 * L.n[0] + 1;
@@ -634,12 +663,12 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
     const int n = L.n[l], N = 2 * n + 1, nv = N * N;
     for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) {
       const int g = k < nv ? k : k - nv;
-      X[l][k] = omega * L.dinv[l][g] * B[l][k];   // dinv and B vanish on the boundary
+      X[l][k] = omega * D[l][g] * B[l][k];   // dinv and B vanish on the boundary
     }
     __syncthreads();
     for (int s = 1; s < pre; ++s) {
       resid(l);
-      for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] += omega * L.dinv[l][k < nv ? k : k - nv] * R[l][k];
+      for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] += omega * D[l][k < nv ? k : k - nv] * R[l][k];
       __syncthreads();
     }
     resid(l);
@@ -676,7 +705,7 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
     // both components per row; column-major inverse: coalesced over r, B read as a broadcast
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
       T acc0 = 0, acc1 = 0;
-      const T* col = Ainv + r;
+      const T* col = Ai + r;
       for (int ky = 0; ky < M; ++ky) {
         const T* b0 = B[l] + (ky + 1) * N + 1;
         for (int kx = 0; kx < M; ++kx, col += m) {
@@ -716,7 +745,7 @@ __global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __
     __syncthreads();
     for (int s = 0; s < post; ++s) {
       resid(l);
-      for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] += omega * L.dinv[l][k < nv ? k : k - nv] * R[l][k];
+      for (int k = threadIdx.x; k < 2 * nv; k += blockDim.x) X[l][k] += omega * D[l][k < nv ? k : k - nv] * R[l][k];
       __syncthreads();
     }
   }
@@ -759,17 +788,27 @@ __device__ void cq1_residual(int n, T hx, T hy, const T* X, const T* B, T* R) {
 template <class T>
 __global__ void __launch_bounds__(1024) k_q1_coarse_vc(CoarseQ1<T> L, const T* __restrict__ Apinv, int m,
                                                         const T* __restrict__ bin, T* __restrict__ xout, T omega,
-                                                        const int* done) {
+                                                        const int* done, int ainv_smem) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   extern __shared__ __align__(16) unsigned char smraw[];
   T* sm = reinterpret_cast<T*>(smraw);
-  T *X[CMAXL], *B[CMAXL], *R[CMAXL];
+  // per level X, B, R and the inverse diagonal (staged once), then the dense pseudo-inverse when it fits
+  T *X[CMAXL], *B[CMAXL], *R[CMAXL], *D[CMAXL];
   size_t off = 0;
   for (int l = 0; l < L.nlev; ++l) {
     const int M = L.n[l] + 1;
     X[l] = sm + off; off += M * M;
     B[l] = sm + off; off += M * M;
     R[l] = sm + off; off += M * M;
+    D[l] = sm + off; off += M * M;
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) D[l][k] = L.dinv[l][k];
+  }
+  const T* Apinv_s = Apinv;
+  if (ainv_smem) {
+    T* sa = sm + off;
+    for (int k = threadIdx.x; k < m * m; k += blockDim.x) sa[k] = Apinv[k];
+    Apinv_s = sa;
   }
   {
     const int M = L.n[0] + 1;
@@ -778,7 +817,7 @@ __global__ void __launch_bounds__(1024) k_q1_coarse_vc(CoarseQ1<T> L, const T* _
   __syncthreads();
   for (int l = 0; l < L.nlev - 1; ++l) {
     const int n = L.n[l], M = n + 1;
-    for (int k = threadIdx.x; k < M * M; k += blockDim.x) X[l][k] = omega * L.dinv[l][k] * B[l][k];
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) X[l][k] = omega * D[l][k] * B[l][k];
     __syncthreads();
     cq1_residual<T>(n, L.hx[l], L.hy[l], X[l], B[l], R[l]);
     const int Mc = L.n[l + 1] + 1;
@@ -802,7 +841,7 @@ __global__ void __launch_bounds__(1024) k_q1_coarse_vc(CoarseQ1<T> L, const T* _
     const int l = L.nlev - 1;
     for (int r = threadIdx.x; r < m; r += blockDim.x) {
       T acc = 0;
-      for (int k = 0; k < m; ++k) acc += Apinv[(size_t)k * m + r] * B[l][k];
+      for (int k = 0; k < m; ++k) acc += Apinv_s[(size_t)k * m + r] * B[l][k];
       X[l][r] = acc;
     }
     __syncthreads();
@@ -816,7 +855,7 @@ __global__ void __launch_bounds__(1024) k_q1_coarse_vc(CoarseQ1<T> L, const T* _
     }
     __syncthreads();
     cq1_residual<T>(n, L.hx[l], L.hy[l], X[l], B[l], R[l]);
-    for (int k = threadIdx.x; k < M * M; k += blockDim.x) X[l][k] += omega * L.dinv[l][k] * R[l][k];
+    for (int k = threadIdx.x; k < M * M; k += blockDim.x) X[l][k] += omega * D[l][k] * R[l][k];
     __syncthreads();
   }
   {
@@ -829,6 +868,7 @@ __global__ void __launch_bounds__(1024) k_q1_coarse_vc(CoarseQ1<T> L, const T* _
 template <class T>
 __global__ void k_q1_jr(int n, T hx, T hy, T omega, const T* __restrict__ dinv, const T* __restrict__ b,
                         T* __restrict__ x, T* __restrict__ r, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int M = n + 1;
   const T rxy = hy / hx, ryx = hx / hy;
@@ -856,6 +896,7 @@ template <class T>
 __global__ void k_q1_ps(int n, T hx, T hy, T omega, const T* __restrict__ dinv, const T* __restrict__ b,
                         const T* __restrict__ x, const T* __restrict__ xc, T* __restrict__ y, const int* done,
                         int sums, Slot sl, int soff) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   T s0 = 0, s1 = 0;
   const int M = n + 1, Mc = n / 2 + 1;
@@ -1144,15 +1185,19 @@ static eth_status q2_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, int pre, int
     C.n[l] = L.n; C.hx[l] = (T)L.hx; C.hy[l] = (T)L.hy; C.nu[l] = (T)L.nu; C.sd[l] = (T)L.sd;
     C.dinv[l] = L.dinv; C.w[l] = L.w;
     const size_t N = 2 * (size_t)L.n + 1;
-    smem += 3 * 2 * N * N * sizeof(T);
+    smem += (3 * 2 + 1 + ((FL & QF_CONV) ? 2 : 0)) * N * N * sizeof(T);
   }
+  const size_t ainv_bytes = (size_t)H.ncoarse * H.ncoarse * sizeof(T);
+  const int ainv_smem = (ainv_bytes <= 48 * 1024 && smem + ainv_bytes <= 200 * 1024) ? 1 : 0;
+  if (ainv_smem) smem += ainv_bytes;
   static size_t set = 0;   // largest dynamic shared memory requested so far (static shared memory counts too)
   if (smem > 200 * 1024) { set_error("multigrid: coarse levels exceed shared memory"); return ETH_EINVAL; }
   if (smem > set) {
     ETH_CUDA(cudaFuncSetAttribute(k_q2_coarse_vc<T, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     set = smem;
   }
-  k_q2_coarse_vc<T, FL><<<1, 512, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, pre, post, done);
+  k_q2_coarse_vc<T, FL><<<1, 512, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, pre, post, done,
+                                                  ainv_smem);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
   return ETH_OK;
@@ -1230,15 +1275,19 @@ static eth_status q1_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, const int* d
     const Level<T>& L = H.lv[Lc + l];
     C.n[l] = L.n; C.hx[l] = (T)L.hx; C.hy[l] = (T)L.hy; C.dinv[l] = L.dinv;
     const size_t M = (size_t)L.n + 1;
-    smem += 3 * M * M * sizeof(T);
+    smem += 4 * M * M * sizeof(T);
   }
+  const size_t ainv_bytes = (size_t)H.ncoarse * H.ncoarse * sizeof(T);
+  const int ainv_smem = (ainv_bytes <= 48 * 1024 && smem + ainv_bytes <= 200 * 1024) ? 1 : 0;
+  if (ainv_smem) smem += ainv_bytes;
   static size_t set = 0;
   if (smem > 200 * 1024) { set_error("multigrid: Q1 coarse levels exceed shared memory"); return ETH_EINVAL; }
   if (smem > set) {
     ETH_CUDA(cudaFuncSetAttribute(k_q1_coarse_vc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     set = smem;
   }
-  k_q1_coarse_vc<T><<<1, 1024, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, done);
+  k_q1_coarse_vc<T><<<1, 1024, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, done,
+                                              ainv_smem);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
   return ETH_OK;

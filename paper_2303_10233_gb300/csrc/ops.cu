@@ -214,6 +214,7 @@ eth_status op_apply_tiles(eth_grid* g, bool fp32, const double* x, double* y, Sl
 // adjoint gradients: grad_f = M_v D_I l_u ; grad_nu = -(D_I l_u)^T A u
 // ---------------------------------------------------------------------------
 __global__ void k_keep_interior(int n, const double* __restrict__ src, double* __restrict__ dst) {
+  ETH_GRID_DEP_WAIT();
   const int N = 2 * n + 1;
   const size_t nv = (size_t)N * N;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
@@ -249,6 +250,7 @@ eth_status grad_kernels(eth_grid* g, const double* lu, const double* u, double* 
 // ---------------------------------------------------------------------------
 __global__ void k_rhs_combine(int n, const double* __restrict__ mf, const double* __restrict__ fub,
                               const double* __restrict__ ub, double* __restrict__ bu) {
+  ETH_GRID_DEP_WAIT();
   const int N = 2 * n + 1;
   const size_t nv = (size_t)N * N;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
@@ -260,6 +262,7 @@ __global__ void k_rhs_combine(int n, const double* __restrict__ mf, const double
 }
 
 __global__ void k_keep_boundary(int n, const double* __restrict__ src, double* __restrict__ dst) {
+  ETH_GRID_DEP_WAIT();
   const int N = 2 * n + 1;
   const size_t nv = (size_t)N * N;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
@@ -271,6 +274,7 @@ __global__ void k_keep_boundary(int n, const double* __restrict__ src, double* _
 }
 
 __global__ void k_scale(size_t m, double a, double* __restrict__ x) {
+  ETH_GRID_DEP_WAIT();
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) x[k] *= a;
 }
 

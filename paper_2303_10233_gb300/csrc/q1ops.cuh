@@ -55,6 +55,7 @@ __host__ __device__ constexpr double q1k(int a, int b) { return a == b ? 1.0 : -
 
 template <class TI, class TO, class CT, int EPI>
 __global__ void __launch_bounds__(256) k_q1node(Q1Params<TI, TO, CT> P) {
+  ETH_GRID_DEP_WAIT();
   if (P.done != nullptr && *P.done) return;
   const int n = P.n, M = n + 1;
   const int tot = M * M;
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(256) k_q1node(Q1Params<TI, TO, CT> P) {
 template <class TI, class TO, class CT>
 __global__ void k_p0rows(int n, CT area, CT cr, CT cq, const TI* __restrict__ x1, const TI* __restrict__ x0,
                          TO* __restrict__ y0, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int tot = n * n, M = n + 1;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x) {

@@ -47,6 +47,7 @@ constexpr size_t q2p_smem_bytes(bool conv) { return 2 * q2p_buf_bytes(conv) + (s
 
 template <int F>
 __global__ void __launch_bounds__(Q2T) k_q2p(Q2Params<double, double, float> P, int ntx, int ntiles) {
+  ETH_GRID_DEP_WAIT();
   using CT = float;
   constexpr bool CONV = F & QF_CONV, XIN = F & QF_XIN, PIN = F & QF_PIN, HP0 = F & QF_P0, UOUT = F & QF_UOUT,
                  POUT = F & QF_POUT, DOT = F & QF_DOT;

@@ -114,7 +114,9 @@ __device__ __forceinline__ CT cvt_stage(TI v, bool valid) {
 }
 
 // FP32 -> FP64 of kernel outputs: the conversion instruction (FP64 pipe, idle in
-// FP32 element kernels) or the integer bit path (ALU pipe).
+// FP32 element kernels) or the integer bit path (ALU pipe).  The operator apply
+// converts its first velocity component one way and the second the other,
+// which balances the two pipes.
 template <class TO, class CT>
 __device__ __forceinline__ TO cvt_out(CT v) {
 #if ETH_OUT_HWCVT
@@ -296,8 +298,13 @@ __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9
 
 // TY = element rows per CTA (tile 32 x TY computed, 31 x (TY-1) owned); the
 // constants below shadow the default-shape ones of the namespace.
+// The FP32 operator apply without convection (32 x 8) is held to 5 resident CTAs
+// per SM (<= 51 registers, no spills): the extra warps hide the staging loads
+// (measured faster than the 4 CTAs that 64 registers allow).
 template <class TI, class TO, class CT, int F, int EPI, int TY = ETH_TEY>
-__global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
+__global__ void __launch_bounds__(TEX * TY, (TY == 8 && EPI == EPI_APPLY && sizeof(CT) == 4 && !(F & QF_CONV)) ? 5 : 1)
+    k_q2(Q2Params<TI, TO, CT> P) {
+  ETH_GRID_DEP_WAIT();
   constexpr int TEY = TY, OEY = TY - 1, Q2T = TEX * TY, SQY = 2 * TY + 1, SPY = TY + 1;
   constexpr bool CONV = F & QF_CONV, XIN = F & QF_XIN, PIN = F & QF_PIN, HP0 = F & QF_P0,
                  UOUT = F & QF_UOUT, POUT = F & QF_POUT, DOT = F & QF_DOT, NOBC = F & QF_NOBC,
@@ -311,7 +318,7 @@ __global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
   CT* eo = sp0 + TEY * TEX;                                 // [NEO][Q2T]
 
   const int n = P.n, N = 2 * n + 1;
-  const size_t nv = (size_t)N * N;
+  const int nv = N * N;   // 32-bit offsets: 2 N_v + N_1 + N_0 < 2^31 for n <= 8192
   const int n1 = (n + 1) * (n + 1);
   const int ex0 = blockIdx.x * OEX, ey0 = blockIdx.y * OEY;
   const int gi0 = 2 * (ex0 - 1), gj0 = 2 * (ey0 - 1);
@@ -331,7 +338,7 @@ __global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
       const int i = gi0 + li, j = gj0 + lj;
       v0[r] = 0; v1[r] = 0; w0[r] = 0; w1[r] = 0; ok[r] = false;
       if (k < SQY * SQX && i >= 0 && i < N && j >= 0 && j < N) {
-        const size_t g = (size_t)j * N + i;
+        const int g = j * N + i;
         const bool bnd = !NOBC && (i == 0 || j == 0 || i == N - 1 || j == N - 1);
         if (XIN && !bnd) {
           ok[r] = true;
@@ -360,14 +367,14 @@ __global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
         const int lj = k / SQX, li = k - lj * SQX;
         const int i = gi0 + li, j = gj0 + lj;
         CT a = 0, b = 0;
-        if (i >= 0 && i < N && j >= 0 && j < N) { const size_t g = (size_t)j * N + i; a = P.w[g]; b = P.w[g + nv]; }
+        if (i >= 0 && i < N && j >= 0 && j < N) { const int g = j * N + i; a = P.w[g]; b = P.w[g + nv]; }
         sw[k] = a; sw[SQY * SQX + k] = b;
       }
     }
     if (XPC) {
       // coarse lattice (level n/2 has 2*(n/2)+1 = n+1 nodes per direction) covering the fine tile
       const int Nc = n + 1;
-      const size_t nvc = (size_t)Nc * Nc;
+      const int nvc = Nc * Nc;
       const int cI0 = 2 * (gi0 >= 0 ? gi0 / 4 : -1), cJ0 = 2 * (gj0 >= 0 ? gj0 / 4 : -1);
       constexpr int CXW = (SQX + 3) / 2 + 4, CYW = (SQY + 3) / 2 + 4;
       CT* sc = eo;   // scratch: eo is unused until phase 1
@@ -376,7 +383,7 @@ __global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
         const int lj = k / CXW, li = k - lj * CXW;
         const int I = cI0 + li, J = cJ0 + lj;
         CT a = 0, b = 0;
-        if (I >= 0 && I < Nc && J >= 0 && J < Nc) { const size_t c = (size_t)J * Nc + I; a = P.xc[c]; b = P.xc[c + nvc]; }
+        if (I >= 0 && I < Nc && J >= 0 && J < Nc) { const int c = J * Nc + I; a = P.xc[c]; b = P.xc[c + nvc]; }
         sc[k] = a; sc[CYW * CXW + k] = b;
       }
       __syncthreads();
@@ -421,12 +428,12 @@ __global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
       const int k = tid + r * Q2T;
       const int lj = k / SPX, li = k - lj * SPX;
       const int I = ex0 - 1 + li, J = ey0 - 1 + lj;
-      pv[r] = (k < SPY * SPX && I >= 0 && I <= n && J >= 0 && J <= n) ? P.p[(size_t)J * (n + 1) + I] : TI(0);
+      pv[r] = (k < SPY * SPX && I >= 0 && I <= n && J >= 0 && J <= n) ? P.p[J * (n + 1) + I] : TI(0);
     }
     if (HP0) {
       const int ly = tid / TEX, lx = tid - ly * TEX;
       const int ex = ex0 - 1 + lx, ey = ey0 - 1 + ly;
-      if (ex >= 0 && ex < n && ey >= 0 && ey < n) p0v = P.p[n1 + (size_t)ey * n + ex];
+      if (ex >= 0 && ex < n && ey >= 0 && ey < n) p0v = P.p[n1 + ey * n + ex];
       sp0[tid] = cvt<CT, TI>(p0v);
     }
 #pragma unroll
@@ -491,14 +498,14 @@ __global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
     const int tL = tid - 1, tB = tid - TEX, tLB = tid - TEX - 1;
     auto E = [&](int a, int b, int t, int c) -> CT { return eo[(c * 9 + b * 3 + a) * Q2T + t]; };
     auto emit = [&](int i, int j, CT s0, CT s1) {
-      const size_t g = (size_t)j * N + i;
+      const int g = j * N + i;
       const bool bnd = !NOBC && (i == 0 || j == 0 || i == N - 1 || j == N - 1);
       const int li = i - gi0, lj = j - gj0;
       TO o0, o1;
       if (EPI == EPI_APPLY) {
         if (bnd) {
           if (XIN) { o0 = (TO)P.x[g]; o1 = (TO)P.x[g + nv]; } else { o0 = 0; o1 = 0; }
-        } else { o0 = cvt_out<TO, CT>(s0); o1 = cvt_out<TO, CT>(s1); }
+        } else { o0 = cvt_out<TO, CT>(s0); o1 = cvt<TO, CT>(s1); }   // FP64 pipe / ALU pipe
       } else if (EPI == EPI_SMOOTH) {
         if (bnd) { if (P.bsrc) { o0 = (TO)P.bsrc[g]; o1 = (TO)P.bsrc[g + nv]; } else { o0 = 0; o1 = 0; } }
         else {
@@ -552,7 +559,7 @@ __global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
     if (POUT && own) {
       auto Q = [&](int cc, int dd, int t) -> CT { return eo[(18 + dd * 2 + cc) * Q2T + t]; };
       auto pemit = [&](int I, int J, CT v) {
-        const size_t gp = (size_t)J * (n + 1) + I;
+        const int gp = J * (n + 1) + I;
         const TO so = cvt_out<TO, CT>(v);
         P.yp[gp] = so;
         if (DOT) dacc += (double)so * (double)P.dvp[gp];
@@ -562,7 +569,7 @@ __global__ void __launch_bounds__(TEX * TY) k_q2(Q2Params<TI, TO, CT> P) {
       if (ey == n - 1) pemit(ex, ey + 1, Q(1, 1, tL) + Q(0, 1, tid));
       if (ex == n - 1 && ey == n - 1) pemit(ex + 1, ey + 1, Q(1, 1, tid));
       if (HP0) {
-        const size_t ge = (size_t)n1 + (size_t)ey * n + ex;
+        const int ge = n1 + ey * n + ex;
         const TO so = cvt_out<TO, CT>(eo[22 * Q2T + tid]);
         P.yp[ge] = so;
         if (DOT) dacc += (double)so * (double)P.dvp[ge];

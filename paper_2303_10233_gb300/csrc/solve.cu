@@ -81,6 +81,7 @@ Slot slot_of(eth_grid* g, int which, int total, int op) {
 // FP64 vector kernels (grid-stride, fused reductions through Slot)
 // ---------------------------------------------------------------------------
 __global__ void k_residual(size_t m, const double* __restrict__ b, const double* __restrict__ y, double* __restrict__ r, Slot sl) {
+  ETH_GRID_DEP_WAIT();
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
     const double v = b[k] - y[k];
@@ -93,16 +94,19 @@ __global__ void k_residual(size_t m, const double* __restrict__ b, const double*
 
 // x_p1 -= sum_p1 / n1 ; x_p0 -= sum_p0 / n0  (sums in sums[0], sums[1])
 __global__ void k_psub(size_t off, size_t n1, size_t n0, double* __restrict__ x, const double* __restrict__ sums) {
+  ETH_GRID_DEP_WAIT();
   const double m1 = sums[0] / (double)n1, m0 = sums[1] / (double)n0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1 + n0; k += (size_t)gridDim.x * blockDim.x)
     x[off + k] -= k < n1 ? m1 : m0;
 }
 
 __global__ void k_add(size_t m, double* __restrict__ x, const double* __restrict__ d) {
+  ETH_GRID_DEP_WAIT();
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) x[k] += d[k];
 }
 
 __global__ void k_set_boundary(int n, double* __restrict__ u, const double* __restrict__ ub) {
+  ETH_GRID_DEP_WAIT();
   const int N = 2 * n + 1;
   const size_t nv = (size_t)N * N;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < 2 * nv; k += (size_t)gridDim.x * blockDim.x) {
@@ -115,6 +119,7 @@ __global__ void k_set_boundary(int n, double* __restrict__ u, const double* __re
 // MINRES v_{j+1} = VA K z_j - VB v_j - VC v_{j-1} (into vo); sums of its p1/p0 blocks.
 __global__ void k_minres_v(size_t nt, size_t nu2, size_t n1, const double* __restrict__ Kz, const double* __restrict__ vj,
                            double* __restrict__ vo, const Scalars* __restrict__ sc, Slot sl) {
+  ETH_GRID_DEP_WAIT();
   if (sc->done) return;
   const double a = sc->v[S_VA], b = sc->v[S_VB], c = sc->v[S_VC];
   double a1 = 0.0, a0 = 0.0;
@@ -130,6 +135,7 @@ __global__ void k_minres_v(size_t nt, size_t nu2, size_t n1, const double* __res
 // MINRES w_{j+1} = WZ z_j - WO w_{j-1} - WW w_j (into wo); x += XC w_{j+1}; last block: done = pending.
 __global__ void k_minres_wx(size_t nt, const double* __restrict__ zj, double* __restrict__ wo, const double* __restrict__ wj,
                             double* __restrict__ x, Scalars* __restrict__ sc, Slot sl) {
+  ETH_GRID_DEP_WAIT();
   if (sc->done) return;
   const double cz = sc->v[S_WZ], co = sc->v[S_WO], cw = sc->v[S_WW], cx = sc->v[S_XC];
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
@@ -149,6 +155,7 @@ __global__ void k_minres_wx(size_t nt, const double* __restrict__ zj, double* __
 __global__ void k_minres_vwx(size_t nt, size_t nu2, size_t n1, const double* __restrict__ Kz, const double* __restrict__ vj,
                              double* __restrict__ vo, const double* __restrict__ zprev, double* __restrict__ wold,
                              const double* __restrict__ wcur, double* __restrict__ x, Scalars* __restrict__ sc, Slot sl) {
+  ETH_GRID_DEP_WAIT();
   if (sc->done) return;
   const double a = sc->v[S_VA], b = sc->v[S_VB], c = sc->v[S_VC];
   const bool wx = sc->v[S_WXP] != 0.0;
@@ -171,6 +178,7 @@ __global__ void k_minres_vwx(size_t nt, size_t nu2, size_t n1, const double* __r
 // the w/x update left pending when the iteration loop stops (applied iff pending)
 __global__ void k_minres_wx_tail(size_t nt, const double* __restrict__ zj, double* __restrict__ wo, const double* __restrict__ wj,
                                  double* __restrict__ x, Scalars* __restrict__ sc) {
+  ETH_GRID_DEP_WAIT();
   if (sc->v[S_WXP] == 0.0) return;
   const double cz = sc->v[S_WZ], co = sc->v[S_WO], cw = sc->v[S_WW], cx = sc->v[S_XC];
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
@@ -180,9 +188,11 @@ __global__ void k_minres_wx_tail(size_t nt, const double* __restrict__ zj, doubl
   }
 }
 
-__global__ void k_minres_wx_clear(Scalars* sc) { sc->v[S_WXP] = 0.0; }
+__global__ void k_minres_wx_clear(Scalars* sc) {
+  ETH_GRID_DEP_WAIT(); sc->v[S_WXP] = 0.0; }
 
 __global__ void k_init_scalars(Scalars* sc, double tol, double n1, double n0, double mqc, double nu) {
+  ETH_GRID_DEP_WAIT();
   for (int k = 0; k < S_LAST; ++k) sc->v[k] = 0.0;
   sc->v[S_TOL] = tol;
   sc->v[S_NP1] = n1;
@@ -206,6 +216,7 @@ template <class T>
 __global__ void k_mq_t(int n, const double* __restrict__ vp, const Scalars* __restrict__ sc, T* __restrict__ b,
                        T* __restrict__ x, const T* __restrict__ dinv, T omega, const int* done,
                        int sums, Slot sl, T inv_area) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int M = n + 1, n1 = M * M;
   const T beta = (T)sc->v[S_BETA];
@@ -229,6 +240,7 @@ __global__ void k_mq_t(int n, const double* __restrict__ vp, const Scalars* __re
 // sums for the k-orthogonality constant: (sum z~, sum_T sum_{I in T} z~_I, sum_T (v0_T + beta)/|T|)
 template <class T>
 __global__ void k_mq_sums(int n, const T* __restrict__ zt, const double* __restrict__ vp, T inv_area, Slot sl, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int M = n + 1, n1 = M * M, n0 = n * n;
   const T beta = (T)sl.sc->v[S_BETA];
@@ -251,6 +263,7 @@ __global__ void k_mq_sums(int n, const T* __restrict__ zt, const double* __restr
 template <class T>
 __global__ void k_mq_out(int n, const T* __restrict__ zt, const double* __restrict__ vp, double* __restrict__ zp, T inv_area,
                          const Scalars* __restrict__ sc, Slot gsl, int goff, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int M = n + 1, n1 = M * M, n0 = n * n;
   const T beta = (T)sc->v[S_BETA], c = (T)sc->v[S_MQC], g1 = (T)sc->v[S_MQG], nu = (T)sc->v[S_MQNU];
@@ -328,6 +341,7 @@ template eth_status precond_pressure<double>(eth_grid*, Hier<double>&, const dou
 // whole outer iteration stays capturable in a CUDA graph.
 // ---------------------------------------------------------------------------
 __global__ void k_pcg_setup(Scalars* sc, int base, int flag, double tol) {
+  ETH_GRID_DEP_WAIT();
   sc->v[base + P_TOL] = tol;
   sc->v[base + P_ITS] = 0.0;
   sc->idone[flag] = sc->done;
@@ -335,6 +349,7 @@ __global__ void k_pcg_setup(Scalars* sc, int base, int flag, double tol) {
 
 __global__ void k_pcg_start(size_t m, const double* __restrict__ b, double* __restrict__ r, double* __restrict__ x,
                             const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (*done) return;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
     r[k] = b[k];
@@ -344,6 +359,7 @@ __global__ void k_pcg_start(size_t m, const double* __restrict__ b, double* __re
 
 // (<a,b>, <a,a>) -> finisher
 __global__ void k_dot2(size_t m, const double* __restrict__ a, const double* __restrict__ b, Slot sl, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (*done) return;
   double s0 = 0.0, s1 = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
@@ -355,6 +371,7 @@ __global__ void k_dot2(size_t m, const double* __restrict__ a, const double* __r
 }
 
 __global__ void k_pcg_copy(size_t m, const double* __restrict__ a, double* __restrict__ b, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (*done) return;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) b[k] = a[k];
 }
@@ -362,6 +379,7 @@ __global__ void k_pcg_copy(size_t m, const double* __restrict__ a, double* __res
 // x += alpha p ; r -= alpha q ; <r, r> -> FIN_PCG_RR
 __global__ void k_pcg_xr(size_t m, const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
                          double* __restrict__ r, Slot sl, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (*done) return;
   const double a = sl.sc->v[sl.base + P_ALPHA];
   double acc = 0.0;
@@ -378,6 +396,7 @@ __global__ void k_pcg_xr(size_t m, const double* __restrict__ p, const double* _
 // p = z + beta p
 __global__ void k_pcg_pupd(size_t m, const double* __restrict__ z, double* __restrict__ p, const Scalars* sc, int base,
                            const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (*done) return;
   const double bt = sc->v[base + P_BETA];
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) p[k] = z[k] + bt * p[k];
@@ -385,6 +404,7 @@ __global__ void k_pcg_pupd(size_t m, const double* __restrict__ z, double* __res
 
 // <a, b> -> finisher
 __global__ void k_dot1(size_t m, const double* __restrict__ a, const double* __restrict__ b, Slot sl, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (*done) return;
   double s0 = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) s0 += a[k] * b[k];
@@ -394,11 +414,13 @@ __global__ void k_dot1(size_t m, const double* __restrict__ a, const double* __r
 
 template <class T>
 __global__ void k_to_t(int m, const double* __restrict__ a, T* __restrict__ b, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (*done) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) b[k] = cvt<T, double>(a[k]);
 }
 template <class T>
 __global__ void k_from_t(int m, const T* __restrict__ a, double* __restrict__ b, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (*done) return;
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) b[k] = cvt<double, T>(a[k]);
 }
@@ -406,6 +428,7 @@ __global__ void k_from_t(int m, const T* __restrict__ a, double* __restrict__ b,
 // t = (r_k - beta) - 1/4 sum_{T ni I} (r_0,T + beta)  in FP64
 __global__ void k_mq_t64(int n, const double* __restrict__ vp, const Scalars* __restrict__ sc, double* __restrict__ t,
                          const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   const int M = n + 1, n1 = M * M;
   const double beta = sc->v[S_BETA];
@@ -554,6 +577,7 @@ static eth_status precond_pressure_exact(eth_grid* g, Work* w, const eth_opts* o
 // exact velocity block with the fused <z_u, v_u> partials into the gamma slot
 __global__ void k_vel_out(size_t m, const double* __restrict__ x, const double* __restrict__ v, double* __restrict__ z,
                           Slot gsl, const int* done) {
+  ETH_GRID_DEP_WAIT();
   if (done != nullptr && *done) return;
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
@@ -614,6 +638,42 @@ static eth_status minres_iter(eth_grid* g, Work* w, const eth_opts* o, bool fp32
   return ETH_OK;
 }
 
+// Programmatic dependent launch inside the captured graphs (ETH_PDL=1 in the
+// environment): every kernel -> kernel edge becomes a programmatic edge from the
+// upstream kernel's launch-completion port, so the downstream grid is scheduled
+// while the upstream one runs and waits in griddepcontrol.wait (first statement
+// of every kernel) for its completion.  Off by default: measured on GB300 it
+// cost 3 % at n = 256 and gained 1 % at n = 512 (the waiting CTAs hold SM slots
+// the producer's blocks could use).
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("ETH_PDL");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+
+eth_status make_programmatic(cudaGraph_t graph) {
+  size_t ne = 0;
+  ETH_CUDA(cudaGraphGetEdges(graph, nullptr, nullptr, nullptr, &ne));
+  if (ne == 0) return ETH_OK;
+  std::vector<cudaGraphNode_t> from(ne), to(ne);
+  std::vector<cudaGraphEdgeData> ed(ne);
+  ETH_CUDA(cudaGraphGetEdges(graph, from.data(), to.data(), ed.data(), &ne));
+  for (size_t k = 0; k < ne; ++k) {
+    cudaGraphNodeType ta, tb;
+    ETH_CUDA(cudaGraphNodeGetType(from[k], &ta));
+    ETH_CUDA(cudaGraphNodeGetType(to[k], &tb));
+    if (ta != cudaGraphNodeTypeKernel || tb != cudaGraphNodeTypeKernel || ed[k].type != cudaGraphDependencyTypeDefault) continue;
+    ETH_CUDA(cudaGraphRemoveDependencies(graph, &from[k], &to[k], &ed[k], 1));
+    cudaGraphEdgeData p{};
+    p.from_port = cudaGraphKernelNodePortLaunchCompletion;
+    p.type = cudaGraphDependencyTypeProgrammatic;
+    ETH_CUDA(cudaGraphAddDependencies(graph, &from[k], &to[k], &p, 1));
+  }
+  return ETH_OK;
+}
+
 eth_status read_scalars(eth_grid* g) {
   ETH_CUDA(cudaMemcpyAsync(g->sch, g->sc, sizeof(Scalars), cudaMemcpyDeviceToHost, g->s));
   ETH_CUDA(cudaStreamSynchronize(g->s));
@@ -663,6 +723,10 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
         g->launches = l0;
         if (st != ETH_OK) return st;
         ETH_CUDA(ce);
+        if (pdl_enabled()) {
+          const eth_status ps = make_programmatic(graph);
+          if (ps != ETH_OK) { cudaGraphDestroy(graph); return ps; }
+        }
         ETH_CUDA(cudaGraphInstantiate(&w->gexec, graph, 0));
         cudaGraphDestroy(graph);
         w->gkey = key;

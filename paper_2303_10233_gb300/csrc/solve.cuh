@@ -30,6 +30,7 @@ struct Work {
 // sums of the Q1 and P0 pressure blocks of x (offset off): FIN_* of (sum p1, sum p0)
 template <int D>
 __global__ void k_psums(size_t off, size_t n1, size_t n0, const double* __restrict__ x, Slot sl) {
+  ETH_GRID_DEP_WAIT();
   double a1 = 0.0, a0 = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1 + n0; k += (size_t)gridDim.x * blockDim.x) {
     if (k < n1) a1 += x[off + k]; else a0 += x[off + k];
