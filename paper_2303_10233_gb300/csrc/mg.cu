@@ -420,7 +420,9 @@ eth_status mg_build_vel(eth_grid* g, Hier<T>& H, int nmin, double art, bool tran
     L.hx = g->hx * (g->n / L.n);
     L.hy = g->hy * (g->n / L.n);
     L.nu = g->nu;
-    L.sd = (l > 0 && conv) ? art : 0.0;
+    // streamline diffusion on every level of the preconditioner's hierarchy (only
+    // where the cell Peclet number exceeds 1); the Krylov method applies the exact F
+    L.sd = conv ? art : 0.0;
     L.trans = trans && conv;
     const size_t N = 2 * (size_t)L.n + 1, nv = N * N;
     ETH_CUDA(cudaMalloc((void**)&L.dinv, nv * sizeof(T)));
@@ -1255,9 +1257,9 @@ template <class T>
 static eth_status vcycle_vel_fused(eth_grid* g, Hier<T>& H, const double* v, double* z, int pre, int post,
                                    const int* done, const Slot* slot, int slot_off, int Lc) {
   const Level<T>& L0 = H.lv[0];
-  // coarse levels carry streamline diffusion (sd > 0), the finest does not (sd = 0 gives delta = 0),
-  // so one instantiation with QF_SD serves all levels.
-  const bool sd = L0.w != nullptr && H.lv.size() > 1 && H.lv[1].sd > 0.0;
+  // every level carries the streamline-diffusion coefficient (delta_T = 0 where the cell
+  // Peclet number is <= 1), so one instantiation with QF_SD serves all levels.
+  const bool sd = L0.w != nullptr && L0.sd > 0.0;
   if (L0.w != nullptr && H.trans && sd) return vcycle_vel_fused_cf<T, QF_CONV | QF_TRANS | QF_SD>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
   if (L0.w != nullptr && H.trans) return vcycle_vel_fused_cf<T, QF_CONV | QF_TRANS>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
   if (sd) return vcycle_vel_fused_cf<T, QF_CONV | QF_SD>(g, H, v, z, pre, post, done, slot, slot_off, Lc);
