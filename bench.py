@@ -158,6 +158,20 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+def aggregate(dist, tot_s, its, device):
+    """Whole-job figures of the replicas: the slowest rank's timed seconds (max over
+    ranks) and the iterations of all ranks (sum); identity without a process group."""
+    if not dist:
+        return tot_s, its
+    import torch
+    tt = torch.tensor([tot_s, its], dtype=torch.float64, device=device)
+    mx = tt.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    sm = tt.clone()
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1])
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -203,13 +217,7 @@ def run_ours(args):
     step_ms = [a.elapsed_time(b) for a, b in evs]
     its = sum(s["iters_total"] for s in stats)
     tot_s = sum(step_ms) / 1e3
-    if dist:
-        tt = torch.tensor([tot_s, its], dtype=torch.float64, device="cuda")
-        mx = tt.clone(); dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = tt.clone(); dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        tot_max, its_all = float(mx[0]), float(sm[1])
-    else:
-        tot_max, its_all = tot_s, its
+    tot_max, its_all = aggregate(dist, tot_s, its, "cuda")
     value = nt * its_all / tot_max / 1e6
     launches = sum(s["kernel_launches"] for s in stats)
 

@@ -98,6 +98,8 @@ typedef struct {
                               residual by less than a factor 2, the next
                               cycles use twice the restart length, up to
                               restart_max (<= 160); 0 or <= restart: fixed  */
+  double mg_omega;         /* damping of the velocity multigrid's Jacobi
+                              smoother (0 < omega < 2); 0: 0.9               */
 } eth_opts;
 
 typedef struct {

@@ -24,6 +24,7 @@
 namespace eth {
 
 constexpr int GM_MAX = 160;
+constexpr int GM_CHUNK = 4;   // graph-replayed Arnoldi steps between host convergence checks
 
 struct GScalars {
   double H[GM_MAX + 1][GM_MAX];
@@ -32,6 +33,7 @@ struct GScalars {
   double res, tol_abs, wnorm, beta;
   double pcg[8];       // inner PCG scalars: rz, pAp, alpha, beta
   int k, done, bdown, skip2;   // skip2: the second Gram-Schmidt pass is not needed
+  int jcur;                    // Arnoldi column of the iteration in flight (graph-replayed loop)
 };
 
 struct GMRESWork {
@@ -55,12 +57,15 @@ struct GMRESWork {
   int pcd_prec = -1;
   int grp = 16;        // basis vectors per pass of the Gram-Schmidt dot kernel (autotuned)
   bool grp_tuned = false;
+  double* vin = nullptr;   // fixed in/out vectors of the graph-replayed Arnoldi step
+  double* zout = nullptr;
 };
 
 void gmres_free(Work* w) {
   GMRESWork* G = w->gm;
   if (!G) return;
   cudaFree(G->V); cudaFree(G->Z); cudaFree(G->w); cudaFree(G->b); cudaFree(G->t);
+  cudaFree(G->vin); cudaFree(G->zout);
   cudaFree(G->gs); if (G->gsh) cudaFreeHost(G->gsh);
   cudaFree(G->part); cudaFree(G->ticket);
   cudaFree(G->c1f); cudaFree(G->c1d); cudaFree(G->mdf); cudaFree(G->mdd); cudaFree(G->q1df); cudaFree(G->q1dd);
@@ -97,9 +102,11 @@ __device__ __forceinline__ bool multi_finish(int nvec, int nb, double* part, uns
 // pass over w: more vectors per pass read w fewer times but hold more accumulators)
 template <int MG_GRP>
 __global__ void k_mdot(size_t n, const double* __restrict__ V, size_t ld, int nvec, const double* __restrict__ w,
-                       double* part, unsigned* ticket, double* out, const int* done, const int* skip, int wnorm) {
+                       double* part, unsigned* ticket, double* out, const int* done, const int* skip, int wnorm,
+                       const int* jp) {
   ETH_GRID_DEP_WAIT();
   if ((done && *done) || (skip && *skip)) return;
+  if (jp) nvec = *jp + 1;   // column index read on the device (graph-replayed loop)
   const int nb = gridDim.x;
   const int nout = nvec + (wnorm ? 1 : 0);
   for (int g0 = 0; g0 < nout; g0 += MG_GRP) {
@@ -151,9 +158,10 @@ __device__ __forceinline__ void arnoldi_finish(GScalars* gs, int j, double wn2) 
 // second pass), otherwise the second pass runs.
 __global__ void k_mupd(size_t n, const double* __restrict__ V, size_t ld, int nvec, const double* __restrict__ h,
                        double* __restrict__ w, int norm, double* part, unsigned* ticket, GScalars* gs, int j, const int* done,
-                       const int* skip) {
+                       const int* skip, const int* jp) {
   ETH_GRID_DEP_WAIT();
   if ((done && *done) || (skip && *skip)) return;
+  if (jp) { j = *jp; nvec = j + 1; }
   double acc = 0.0;
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) {
     double v = w[k];
@@ -183,9 +191,11 @@ __global__ void k_mupd(size_t n, const double* __restrict__ V, size_t ld, int nv
   }
 }
 
-__global__ void k_vscale(size_t n, const double* __restrict__ w, double* __restrict__ v, const GScalars* gs, int use_beta) {
+__global__ void k_vscale(size_t n, const double* __restrict__ w, double* __restrict__ v, const GScalars* gs, int use_beta,
+                         size_t ld = 0, const int* jp = nullptr) {
   ETH_GRID_DEP_WAIT();
   if (gs->done && !use_beta) return;
+  if (jp) v += (size_t)(*jp + 1) * ld;   // next basis column, index read on the device
   const double s = 1.0 / (use_beta ? gs->beta : gs->wnorm);
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) v[k] = s * w[k];
 }
@@ -212,10 +222,29 @@ __global__ void k_gm_resid(size_t n, const double* __restrict__ b, const double*
       gs->res = beta;
       gs->tol_abs = tol_abs;
       gs->k = 0;
+      gs->jcur = 0;
       gs->done = (beta <= tol_abs || !isfinite(beta)) ? 1 : 0;
       gs->bdown = isfinite(beta) ? 0 : 8;
     }
   }
+}
+
+// column jcur of a basis <-> a fixed vector (graph-replayed Arnoldi loop)
+__global__ void k_gm_col_in(size_t n, const double* __restrict__ V, size_t ld, const GScalars* gs, double* __restrict__ out) {
+  ETH_GRID_DEP_WAIT();
+  if (gs->done) return;
+  const double* src = V + (size_t)gs->jcur * ld;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) out[k] = src[k];
+}
+__global__ void k_gm_col_out(size_t n, const double* __restrict__ in, double* __restrict__ Z, size_t ld, const GScalars* gs) {
+  ETH_GRID_DEP_WAIT();
+  if (gs->done) return;
+  double* dst = Z + (size_t)gs->jcur * ld;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n; k += (size_t)gridDim.x * blockDim.x) dst[k] = in[k];
+}
+__global__ void k_gm_next(GScalars* gs) {
+  ETH_GRID_DEP_WAIT();
+  if (!gs->done) gs->jcur += 1;
 }
 
 // y = H(0:k,0:k)^{-1} g(0:k) by back substitution (one thread)
@@ -433,11 +462,11 @@ __global__ void k_oseen_scalars(Scalars* sc, double n1, double n0, double mqc, d
 static int gb(size_t m) { return vblocks(m); }
 
 static eth_status launch_mdot(GMRESWork* G, int nb, cudaStream_t s, size_t ntv, size_t ld, int nvec, double* out,
-                              const int* done, const int* skip, int wnorm) {
+                              const int* done, const int* skip, int wnorm, const int* jp = nullptr) {
   switch (G->grp) {
-    case 4: k_mdot<4><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm); break;
-    case 8: k_mdot<8><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm); break;
-    default: k_mdot<16><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm); break;
+    case 4: k_mdot<4><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm, jp); break;
+    case 8: k_mdot<8><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm, jp); break;
+    default: k_mdot<16><<<nb, 256, 0, s>>>(ntv, G->V, ld, nvec, G->w, G->part, G->ticket + 3, out, done, skip, wnorm, jp); break;
   }
   ETH_CUDA(cudaGetLastError());
   return ETH_OK;
@@ -495,6 +524,8 @@ static eth_status gm_alloc(eth_grid* g, Work* w, int m) {
   ETH_CUDA(cudaMalloc((void**)&G->w, G->cap * 8));
   ETH_CUDA(cudaMalloc((void**)&G->b, G->cap * 8));
   ETH_CUDA(cudaMalloc((void**)&G->t, G->cap * 8));
+  ETH_CUDA(cudaMalloc((void**)&G->vin, G->cap * 8));
+  ETH_CUDA(cudaMalloc((void**)&G->zout, G->cap * 8));
   ETH_CUDA(cudaMalloc((void**)&G->gs, sizeof(GScalars)));
   ETH_CUDA(cudaMallocHost((void**)&G->gsh, sizeof(GScalars)));
   G->nbmax = 152 * 8;
@@ -720,6 +751,37 @@ static eth_status sys_apply(eth_grid* g, int stage, bool fp32, bool trans, const
   return op_apply(g, op, fp32, x, y);
 }
 
+// One Arnoldi step (preconditioner, operator, Gram-Schmidt, normalisation) with the
+// column index read on the device (GScalars::jcur), so the same launches serve
+// every column: this is what the graph-replayed loop captures once per stage.
+template <class T>
+static eth_status gm_iter_kernels(eth_grid* g, Work* w, const eth_opts* o, int stage, bool fp32, bool adj, size_t ntv) {
+  GMRESWork* G = w->gm;
+  const size_t ld = G->cap;
+  const int nb = gb(ntv);
+  const int* done = &G->gs->done;
+  const int* jp = &G->gs->jcur;
+  const int* sk = &G->gs->skip2;
+  double* h1 = &G->gs->h1[0];
+  double* h2 = &G->gs->h2[0];
+  k_gm_col_in<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, G->gs, G->vin);
+  ETH_CUDA(cudaGetLastError());
+  if (stage == 1) ETH_TRY(precond_pcd<T>(g, w, o, G->vin, G->zout, done, adj));
+  else ETH_TRY(precond_m1<T>(g, w, o, G->vin, G->zout, done, adj));
+  k_gm_col_out<<<nb, 256, 0, g->s>>>(ntv, G->zout, G->Z, ld, G->gs);
+  ETH_CUDA(cudaGetLastError());
+  ETH_TRY(sys_apply(g, stage, fp32, adj, G->zout, G->w));
+  ETH_TRY(launch_mdot(G, nb, g->s, ntv, ld, 1, h1, done, nullptr, 1, jp));
+  k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, 1, h1, G->w, 2, G->part, G->ticket + 4, G->gs, 0, done, nullptr, jp);
+  ETH_TRY(launch_mdot(G, nb, g->s, ntv, ld, 1, h2, done, sk, 0, jp));
+  k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, 1, h2, G->w, 1, G->part, G->ticket + 4, G->gs, 0, done, sk, jp);
+  k_vscale<<<nb, 256, 0, g->s>>>(ntv, G->w, G->V, G->gs, 0, ld, jp);
+  k_gm_next<<<1, 1, 0, g->s>>>(G->gs);
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 8;
+  return ETH_OK;
+}
+
 template <class T>
 // Restarted flexible GMRES; every cycle starts from the FP64 residual of the
 // current iterate (a refinement step).  In mixed precision the Arnoldi
@@ -740,6 +802,14 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
   *status = 0;
   *escalated = 0;
   double res = 0.0, res_prev = -1.0;
+  const bool use_graph = o->graph != 0;
+  cudaGraphExec_t gexec = nullptr;
+  int gfp32 = -1;
+  long glaunch = 0;
+  struct GraphGuard {
+    cudaGraphExec_t* e;
+    ~GraphGuard() { if (*e) cudaGraphExecDestroy(*e); }
+  } guard{&gexec};
   while (true) {
     ETH_TRY(sys_apply(g, stage, false, adj, x, G->w));
     k_gm_resid<<<nb, 256, 0, g->s>>>(ntv, b, G->w, G->V, G->part, G->ticket, G->gs, tol_abs);
@@ -766,7 +836,39 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
     g->launches++;
     const int* done = &G->gs->done;
     int kdone = 0;
-    for (int j = 0; j < m && its < maxit; ++j) {
+    if (use_graph) {
+      // the captured Arnoldi step, replayed in chunks; the host checks convergence after
+      // each chunk (steps after the converged one return at once: every kernel checks done)
+      if (!gexec || gfp32 != (int)fp32) {
+        if (gexec) { cudaGraphExecDestroy(gexec); gexec = nullptr; }
+        cudaGraph_t graph;
+        const long l0 = g->launches;
+        ETH_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
+        const eth_status cs = gm_iter_kernels<T>(g, w, o, stage, fp32, adj, ntv);
+        const cudaError_t ce = cudaStreamEndCapture(g->s, &graph);
+        glaunch = g->launches - l0;
+        g->launches = l0;
+        if (cs != ETH_OK) { if (ce == cudaSuccess) cudaGraphDestroy(graph); return cs; }
+        ETH_CUDA(ce);
+        const cudaError_t ie = cudaGraphInstantiate(&gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        ETH_CUDA(ie);
+        gfp32 = (int)fp32;
+      }
+      int j = 0;
+      while (j < m && its < maxit) {
+        const int ch = std::min(GM_CHUNK, std::min(m - j, maxit - its));
+        for (int c = 0; c < ch; ++c) ETH_CUDA(cudaGraphLaunch(gexec, g->s));
+        g->launches += ch * glaunch;
+        ETH_CUDA(cudaMemcpyAsync(&G->gsh->res, &G->gs->res, 4 * sizeof(double), cudaMemcpyDeviceToHost, g->s));
+        ETH_CUDA(cudaMemcpyAsync(&G->gsh->k, &G->gs->k, 4 * sizeof(int), cudaMemcpyDeviceToHost, g->s));
+        ETH_CUDA(cudaStreamSynchronize(g->s));
+        if (G->gsh->done) { its += G->gsh->k - j; break; }
+        j += ch;
+        its += ch;
+      }
+    }
+    for (int j = 0; !use_graph && j < m && its < maxit; ++j) {
       double* Vj = G->V + (size_t)j * ld;
       double* Zj = G->Z + (size_t)j * ld;
       if (stage == 1) ETH_TRY(precond_pcd<T>(g, w, o, Vj, Zj, done, adj));
@@ -777,9 +879,9 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
       // classical Gram-Schmidt with selective reorthogonalisation (DGKS, 0.7)
       const int* sk = &G->gs->skip2;
       ETH_TRY(launch_mdot(G, nb, g->s, ntv, ld, j + 1, h1, done, nullptr, 1));
-      k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h1, G->w, 2, G->part, G->ticket + 4, G->gs, j, done, nullptr);
+      k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h1, G->w, 2, G->part, G->ticket + 4, G->gs, j, done, nullptr, nullptr);
       ETH_TRY(launch_mdot(G, nb, g->s, ntv, ld, j + 1, h2, done, sk, 0));
-      k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h2, G->w, 1, G->part, G->ticket + 4, G->gs, j, done, sk);
+      k_mupd<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, j + 1, h2, G->w, 1, G->part, G->ticket + 4, G->gs, j, done, sk, nullptr);
       k_vscale<<<nb, 256, 0, g->s>>>(ntv, G->w, G->V + (size_t)(j + 1) * ld, G->gs, 0);
       ETH_CUDA(cudaGetLastError());
       g->launches += 5;

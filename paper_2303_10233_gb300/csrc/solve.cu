@@ -764,9 +764,15 @@ eth_status ensure_hier(eth_grid* g, Work* w, const eth_opts* o) {
   Hier<T>& V = vel_hier<T>(w);
   Hier<T>& Q = q1_hier<T>(w);
   if (!V.built) ETH_TRY(mg_build_vel<T>(g, V, nmin, g->kind == ETH_OSEEN ? 0.5 : 0.0, false));
+  const double om = o->mg_omega > 0.0 ? o->mg_omega : 0.9;   // 0.9: fewest iterations, Stokes 256^2 / 512^2
+  if (V.omega != om) {   // the captured graph holds the damping as a kernel argument
+    V.omega = om;
+    if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; w->gkey = -1; }
+  }
   if (g->kind == ETH_OSEEN && w->need_adj) {
     Hier<T>& Vt = vel_hier_t<T>(w);
     if (!Vt.built) ETH_TRY(mg_build_vel<T>(g, Vt, nmin, 0.5, true));
+    Vt.omega = om;
   }
   if (!Q.built) ETH_TRY(mg_build_q1<T>(g, Q, nmin));
   return ETH_OK;
@@ -878,7 +884,10 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   if (!g->has_rhs) { set_error("eth_solve: no right-hand side (eth_set_rhs)"); return ETH_EINVAL; }
   eth_opts o;
   if (opts) o = *opts; else eth_default_opts(&o);
-  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1) { set_error("eth_solve: bad options"); return ETH_EINVAL; }
+  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1 || !(o.mg_omega >= 0.0 && o.mg_omega < 2.0)) {
+    set_error("eth_solve: bad options");
+    return ETH_EINVAL;
+  }
   if ((o.a_exact || o.mq_mode == ETH_MQ_EXACT) && !(o.inner_tol > 0)) { set_error("eth_solve: bad inner_tol"); return ETH_EINVAL; }
   if (o.precision != ETH_FP64 && o.precision != ETH_MIXED) { set_error("eth_solve: bad precision"); return ETH_EINVAL; }
   eth_stats st;
@@ -944,7 +953,10 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
   if (!g->has_coef) { set_error("eth_solve_adjoint: call eth_set_coefficients first"); return ETH_EINVAL; }
   eth_opts o;
   if (opts) o = *opts; else eth_default_opts(&o);
-  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1) { set_error("eth_solve_adjoint: bad options"); return ETH_EINVAL; }
+  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1 || !(o.mg_omega >= 0.0 && o.mg_omega < 2.0)) {
+    set_error("eth_solve_adjoint: bad options");
+    return ETH_EINVAL;
+  }
   eth_stats st;
   std::memset(&st, 0, sizeof(st));
   Work* w;

@@ -35,7 +35,7 @@ class Opts(ctypes.Structure):
                 ("mg_post", ctypes.c_int), ("mg_min_n", ctypes.c_int), ("mq_mode", ctypes.c_int),
                 ("a_exact", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("refine_inner_tol", ctypes.c_double), ("graph", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("restart_max", ctypes.c_int)]
+                ("autotune", ctypes.c_int), ("restart_max", ctypes.c_int), ("mg_omega", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

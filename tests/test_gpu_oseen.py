@@ -42,3 +42,18 @@ def test_oseen_matches_direct(eth, n, nu, precision):
     assert st["iters_stage1"] > 0 and st["iters_stage2"] >= 0
     # Prop. 2 at the switch: ||z*||^2 <= c^2 eta^2 ||f||^2 + ||r0*||^2
     assert st["prop2_lhs"] <= st["prop2_bound"] * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_replayed_gmres_matches_stream_loop(eth, precision):
+    """The graph-replayed Arnoldi step (column index read on the device, chunks of
+    steps between host checks) performs the same arithmetic as the stream loop:
+    same iteration counts and the same iterate, bitwise."""
+    w = W.oseen_cavity(48, nu=1 / 200, seed=3)
+    G = eth.problem(w)
+    u0, p0, s0 = G.solve(tol=1e-8, precision=precision, graph=0)
+    u1, p1, s1 = G.solve(tol=1e-8, precision=precision, graph=1)
+    G.close()
+    assert s0["status"] == 0 and s1["status"] == 0
+    assert (s0["iters_stage1"], s0["iters_stage2"]) == (s1["iters_stage1"], s1["iters_stage2"])
+    assert torch.equal(u0, u1) and torch.equal(p0, p1)
