@@ -57,3 +57,19 @@ def test_graph_replayed_gmres_matches_stream_loop(eth, precision):
     assert s0["status"] == 0 and s1["status"] == 0
     assert (s0["iters_stage1"], s0["iters_stage2"]) == (s1["iters_stage1"], s1["iters_stage2"])
     assert torch.equal(u0, u1) and torch.equal(p0, p1)
+
+
+def test_adaptive_restart_and_option_checks(eth):
+    """restart_max lets slow restart cycles double the restart length: a short
+    GMRES(8) that cannot finish in 600 iterations converges when allowed to grow
+    to 64 (cavity 32x32, nu = 1/200); out-of-range smoother damping is rejected before any device work."""
+    w = W.oseen_cavity(32, nu=1 / 200, seed=2)
+    G = eth.problem(w)
+    _, _, sf = G.solve(tol=1e-8, restart=8, maxit=600)
+    _, _, sa = G.solve(tol=1e-8, restart=8, restart_max=64, maxit=600)
+    assert sa["status"] == 0 and sa["relres_true"] <= 1e-8 * 1.01
+    if sf["status"] == 0:
+        assert sa["iters_total"] <= sf["iters_total"]
+    with pytest.raises(eth.EthError):
+        G.solve(tol=1e-8, mg_omega=2.5)
+    G.close()
