@@ -371,6 +371,21 @@ def profile_apply(n, kind):
     G.close()
 
 
+def profile_solve(n, kind):
+    """Two default solves of the n x n workload (Stokes MMS or Oseen cavity, nu = 1/100)
+    for an ncu launch list of the solver (the second solve is the one to read)."""
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_10233_gb300 import eth, workloads as W
+    w = W.oseen_cavity(n, nu=0.01, seed=1) if kind == "oseen" else W.mms(n, seed=SEED)
+    G = eth.problem(w)
+    for _ in range(2):
+        _, _, st = G.solve(tol=TOL)
+    print(f"profile_solve n={n} kind={kind} its={st['iters_stage1']}+{st['iters_stage2']} "
+          f"ms={st['seconds'] * 1e3:.1f} launches={st['kernel_launches']}")
+    G.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,9 +396,14 @@ def main():
     ap.add_argument("--profile-apply", type=int, default=0, metavar="N",
                     help="only run the fused K apply (FP32 math) 5 times on an N x N grid (for ncu captures)")
     ap.add_argument("--profile-kind", default="stokes", choices=["stokes", "oseen"])
+    ap.add_argument("--profile-solve", type=int, default=0, metavar="N",
+                    help="only run two default solves on an N x N grid of --profile-kind (for ncu launch lists)")
     args = ap.parse_args()
     if args.profile_apply:
         profile_apply(args.profile_apply, args.profile_kind)
+        return
+    if args.profile_solve:
+        profile_solve(args.profile_solve, args.profile_kind)
         return
     if args.impl == "reference":
         run_reference(args)
