@@ -298,11 +298,13 @@ __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9
 
 // TY = element rows per CTA (tile 32 x TY computed, 31 x (TY-1) owned); the
 // constants below shadow the default-shape ones of the namespace.
-// The FP32 operator apply without convection (32 x 8) is held to 5 resident CTAs
-// per SM (<= 51 registers, no spills): the extra warps hide the staging loads
-// (measured faster than the 4 CTAs that 64 registers allow).
+// The FP32 operator apply (32 x 8) is held to 5 resident CTAs per SM without
+// convection (<= 51 registers, no spills) and to 4 with it (<= 64 registers,
+// a few spills): the extra warps hide the staging loads (measured: Stokes
+// 1024^2 57.9 -> 52.7 us; Oseen 1024^2 160 us at the 166 registers the
+// compiler takes unbounded -> 82 us).
 template <class TI, class TO, class CT, int F, int EPI, int TY = ETH_TEY>
-__global__ void __launch_bounds__(TEX * TY, (TY == 8 && EPI == EPI_APPLY && sizeof(CT) == 4 && !(F & QF_CONV)) ? 5 : 1)
+__global__ void __launch_bounds__(TEX * TY, (TY == 8 && EPI == EPI_APPLY && sizeof(CT) == 4) ? ((F & QF_CONV) ? 4 : 5) : 1)
     k_q2(Q2Params<TI, TO, CT> P) {
   ETH_GRID_DEP_WAIT();
   constexpr int TEY = TY, OEY = TY - 1, Q2T = TEX * TY, SQY = 2 * TY + 1, SPY = TY + 1;

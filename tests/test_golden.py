@@ -21,7 +21,7 @@ def _table(name):
 def test_table1_dof_counts():
     """Table 1: velocity and vertex-pressure counts equal the Q2 / Q1 lattice
     sizes of the oracle's grid; the P2-P1* frame adds 2n^2 centroids, the
-    Q2-Q1* frame of this build adds n^2 element constants."""
+    Q2-Q1* frame on quadrilaterals adds n^2 element constants."""
     for lev, nvel, np1, npstar in _table("table1_dofs.txt"):
         n = 2 ** lev
         g = fem.Grid(n)
