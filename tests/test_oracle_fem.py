@@ -171,3 +171,19 @@ def test_dof_counts_match_paper_table():
     assert fem.Grid(16).nu == 2178
     assert W.sizes(256)[1] == 526338
     assert W.sizes(16) == (1089, 2178, 289, 256, 2723)
+
+
+@pytest.mark.parametrize("n,kind", [(6, "stokes"), (8, "oseen"), (10, "oseen")])
+def test_k_rows_equal_assembled_rows(n, kind):
+    """oracle.rows.k_rows (element by element, used for sampled full-size parity)
+    equals the rows of the assembled K, boundary, interior, Q1 and P0 rows alike."""
+    from oracle import rows as R
+    from paper_2303_10233_gb300 import workloads as W
+    w = W.oseen_cavity(n, nu=0.02, seed=4) if kind == "oseen" else W.mms(n, seed=1, nu=0.3)
+    g = fem.Grid(n)
+    s = problem.System(g, w["nu"], w["wind"])
+    x = np.random.default_rng(n).standard_normal(g.nt)
+    ref = s.K @ x
+    rows = np.arange(g.nt)
+    got = R.k_rows(g, w["nu"], w["wind"], x, rows)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
