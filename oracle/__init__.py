@@ -23,6 +23,8 @@ two-level pressure approximation"):
                   M_1 (Eq. nse-precon-ref) and Q1 PCD (Eq.
                   discrete-commutator1x), and the two-stage method (Sec. 3.1).
 * ``adjoint``  -- adjoint solve and gradients w.r.t. body force and viscosity.
+* ``rows``     -- selected entries of K x element by element (no assembly), for
+                  sampled parity at full grid sizes.
 
 Parity pins live in ``tests/test_oracle_*.py``.  Functions with no pin say
 "parity unpinned" in their docstring.

@@ -835,7 +835,6 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
     ETH_CUDA(cudaGetLastError());
     g->launches++;
     const int* done = &G->gs->done;
-    int kdone = 0;
     if (use_graph) {
       // the captured Arnoldi step, replayed in chunks; the host checks convergence after
       // each chunk (steps after the converged one return at once: every kernel checks done)
@@ -886,12 +885,11 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
       ETH_CUDA(cudaGetLastError());
       g->launches += 5;
       its++;
-      ETH_CUDA(cudaMemcpyAsync(&G->gsh->res, &G->gs->res, 4 * sizeof(double) + 0, cudaMemcpyDeviceToHost, g->s));
+      ETH_CUDA(cudaMemcpyAsync(&G->gsh->res, &G->gs->res, 4 * sizeof(double), cudaMemcpyDeviceToHost, g->s));
       ETH_CUDA(cudaMemcpyAsync(&G->gsh->k, &G->gs->k, 4 * sizeof(int), cudaMemcpyDeviceToHost, g->s));
       ETH_CUDA(cudaStreamSynchronize(g->s));
-      if (G->gsh->done) { kdone = 1; break; }
+      if (G->gsh->done) break;
     }
-    (void)kdone;
     k_gm_solve<<<1, 1, 0, g->s>>>(G->gs);
     k_zupd<<<nb, 256, 0, g->s>>>(ntv, G->Z, ld, G->gs, x);
     ETH_CUDA(cudaGetLastError());

@@ -600,8 +600,6 @@ static eth_status precond_stokes(eth_grid* g, Work* w, const eth_opts* o, const 
   if (o->mq_mode == ETH_MQ_EXACT) ETH_TRY(precond_pressure_exact<T>(g, w, o, v + nu2, z + nu2, gs, nbv, done, w->s2));
   else ETH_TRY(precond_pressure<T>(g, q1_hier<T>(w), v + nu2, z + nu2, gs, nbv, done, w->s2));
   if (o->a_exact) {
-    double* xv = w->pcg + 3 * nu2 + 0;   // reuse: result written to z, q buffer as scratch is not needed after
-    (void)xv;
     ETH_TRY(vel_pcg<T>(g, w, o, v, z, 60));
     // <z_u, v_u> partials (z_u already in place)
     k_vel_out<<<nbv, 256, 0, g->s>>>(nu2, z, v, z, gs, done);
@@ -625,7 +623,7 @@ static eth_status minres_iter(eth_grid* g, Work* w, const eth_opts* o, bool fp32
   double* vj = w->V[j & 1];
   double* vo = w->V[(j + 1) & 1];
   double* wj = w->W[j & 1];
-  double* wo = w->W[(j + 1) & 1];
+  double* wo = w->W[(j + 1) & 1];   // w_{j-2}, overwritten by w_j
   ETH_TRY(op_apply_K_dot(g, fp32, false, zj, w->Kz, slot_of(g, SL_DELTA, 0, FIN_MINRES_DELTA), done));
   const int nb = vblocks(nt);
   // v_{j+1} and the pending w/x update of iteration j-1 (z_{j-1} = zn's buffer, not yet overwritten)
@@ -634,7 +632,6 @@ static eth_status minres_iter(eth_grid* g, Work* w, const eth_opts* o, bool fp32
   ETH_CUDA(cudaGetLastError());
   ETH_TRY(precond_stokes<T>(g, w, o, vo, zn, FIN_MINRES_GAMMA, done));
   g->launches += 1;
-  (void)wo;
   return ETH_OK;
 }
 
