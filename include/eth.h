@@ -86,7 +86,11 @@ typedef struct {
   int a_exact;             /* 1: exact velocity solves (inner PCG), P_1 form */
   double inner_tol;        /* inner exact-solve tolerance when exact         */
   double refine_inner_tol; /* mixed: relative tolerance of each inner solve  */
-  int graph;               /* 1: replay captured CUDA graphs                 */
+  int graph;               /* 0: stream launches; 1: CUDA graphs, the MINRES
+                              loop run on the device by a conditional WHILE
+                              node; 2: CUDA graphs of two MINRES iterations
+                              replayed by the host (GMRES: 1 and 2 replay the
+                              captured Arnoldi step)                        */
   int verbose;
   int autotune;            /* 1: before the first solve of a grid, time the
                               fused K apply with tiles of 32 x {4, 8, 16}

@@ -15,6 +15,7 @@ struct Scalars {
   int iter;              // device iteration counter
   int inner_done;        // unused
   int idone[4];          // early-exit flags of inner (nested) PCG solves
+  int loops, max_loops;  // bodies run by the device-side MINRES loop and their cap
 };
 
 // Inner PCG state blocks (exact preconditioner blocks): base index of each.

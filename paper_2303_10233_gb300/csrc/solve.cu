@@ -191,8 +191,21 @@ __global__ void k_minres_wx_tail(size_t nt, const double* __restrict__ zj, doubl
 __global__ void k_minres_wx_clear(Scalars* sc) {
   ETH_GRID_DEP_WAIT(); sc->v[S_WXP] = 0.0; }
 
-__global__ void k_init_scalars(Scalars* sc, double tol, double n1, double n0, double mqc, double nu) {
+// End of one body of the device-side MINRES loop (a conditional WHILE node of the
+// solver graph): run the body again unless converged, broken down or out of
+// iterations.  The body count is capped independently of the solver state, so
+// the loop always ends.
+__global__ void k_minres_loop(cudaGraphConditionalHandle h, Scalars* sc) {
   ETH_GRID_DEP_WAIT();
+  const int l = ++sc->loops;
+  const bool more = !sc->done && sc->status == 0 && l < sc->max_loops;
+  cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+__global__ void k_init_scalars(Scalars* sc, double tol, double n1, double n0, double mqc, double nu, int maxit) {
+  ETH_GRID_DEP_WAIT();
+  sc->loops = 0;
+  sc->max_loops = (maxit + 1) / 2;   // two MINRES iterations per loop body
   for (int k = 0; k < S_LAST; ++k) sc->v[k] = 0.0;
   sc->v[S_TOL] = tol;
   sc->v[S_NP1] = n1;
@@ -683,7 +696,7 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
   const size_t nt = g->nt;
   const double area = g->hx * g->hy;
   k_init_scalars<<<1, 1, 0, g->s>>>(g->sc, tol, (double)g->n1, (double)g->n0,
-                                    o->mq_mode == ETH_MQ_EXACT ? 1.0 : 16.0 / area, g->nu);
+                                    o->mq_mode == ETH_MQ_EXACT ? 1.0 : 16.0 / area, g->nu, maxit);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
   ETH_CUDA(cudaMemsetAsync(w->d, 0, nt * 8, g->s));
@@ -704,31 +717,66 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
   if (g->sch->v[S_PEND] != 0.0) { *its = 0; *dstat = g->sch->status; return ETH_OK; }
   int j = 1;
   const bool use_graph = o->graph != 0;
+  const bool device_loop = o->graph == 1;   // 1: the whole loop on the device; 2: host-checked replays
   const int key = (int)fp32 * 1000 + (int)(sizeof(T)) * 10 + o->mg_pre + 100 * o->mg_post + 10000 * o->a_exact +
-                  20000 * o->mq_mode + 100000 * tile_code(g);
+                  20000 * o->mq_mode + 100000 * tile_code(g) + 10000000 * o->graph;
   while (true) {
     if (use_graph) {
       if (!w->gexec || w->gkey != key) {
         if (w->gexec) { cudaGraphExecDestroy(w->gexec); w->gexec = nullptr; }
-        cudaGraph_t graph;
+        cudaGraph_t graph = nullptr, body = nullptr;
+        cudaGraphConditionalHandle cond = 0;
+        if (device_loop) {
+          // a WHILE conditional node whose body is two MINRES iterations and the loop test
+          ETH_CUDA(cudaGraphCreate(&graph, 0));
+          cudaError_t ge = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+          cudaGraphNodeParams cp{};
+          cp.type = cudaGraphNodeTypeConditional;
+          cp.conditional.handle = cond;
+          cp.conditional.type = cudaGraphCondTypeWhile;
+          cp.conditional.size = 1;
+          cudaGraphNode_t cnode;
+          if (ge == cudaSuccess) ge = cudaGraphAddNode(&cnode, graph, nullptr, nullptr, 0, &cp);
+          if (ge == cudaSuccess) {
+            body = cp.conditional.phGraph_out[0];
+            ge = cudaStreamBeginCaptureToGraph(g->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+          }
+          if (ge != cudaSuccess) { cudaGraphDestroy(graph); return cuda_status(ge, "MINRES loop graph"); }
+        } else {
+          ETH_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
+        }
         const long l0 = g->launches;
-        ETH_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
         eth_status st = minres_iter<T>(g, w, o, fp32, 1);
         if (st == ETH_OK) st = minres_iter<T>(g, w, o, fp32, 2);
-        cudaError_t ce = cudaStreamEndCapture(g->s, &graph);
+        if (st == ETH_OK && device_loop) {
+          k_minres_loop<<<1, 1, 0, g->s>>>(cond, g->sc);
+          if (cudaGetLastError() != cudaSuccess) st = ETH_ECUDA;
+        }
+        cudaGraph_t captured = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(g->s, &captured);
         w->glaunch = g->launches - l0;
         g->launches = l0;
-        if (st != ETH_OK) return st;
-        ETH_CUDA(ce);
+        if (!device_loop) graph = captured;
+        if (st != ETH_OK || ce != cudaSuccess) {
+          if (graph) cudaGraphDestroy(graph);
+          if (st != ETH_OK) return st;
+          ETH_CUDA(ce);
+        }
         if (pdl_enabled()) {
-          const eth_status ps = make_programmatic(graph);
+          const eth_status ps = make_programmatic(device_loop ? body : graph);
           if (ps != ETH_OK) { cudaGraphDestroy(graph); return ps; }
         }
-        ETH_CUDA(cudaGraphInstantiate(&w->gexec, graph, 0));
+        const cudaError_t ie = cudaGraphInstantiate(&w->gexec, graph, 0);
         cudaGraphDestroy(graph);
+        ETH_CUDA(ie);
         w->gkey = key;
       }
       ETH_CUDA(cudaGraphLaunch(w->gexec, g->s));
+      if (device_loop) {
+        ETH_TRY(read_scalars(g));
+        g->launches += (long)g->sch->loops * w->glaunch;
+        break;
+      }
       g->launches += w->glaunch;
     } else {
       ETH_TRY(minres_iter<T>(g, w, o, fp32, j));

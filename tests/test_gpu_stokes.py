@@ -98,3 +98,18 @@ def test_cavity16_exact_blocks_match_oracle_minres(eth):
     assert abs(st["iters_total"] - info["its"]) <= 1, (st["iters_total"], info["its"])
     xd, _ = direct.solve(s, b)
     assert np.linalg.norm(s.canonical(x) - xd) <= 1e-6 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_modes_match_stream_launches(eth, precision):
+    """The device-side MINRES loop (conditional WHILE graph node, graph=1), host-replayed
+    graphs of two iterations (graph=2) and plain stream launches (graph=0) perform the
+    same arithmetic: same iteration count and the same solution, bitwise."""
+    w = W.mms(40, seed=5)
+    G = eth.problem(w)
+    out = [G.solve(tol=1e-8, precision=precision, graph=m) for m in (0, 1, 2)]
+    G.close()
+    (u0, p0, s0) = out[0]
+    for u, p, s in out[1:]:
+        assert s["status"] == 0 and s["iters_total"] == s0["iters_total"]
+        assert torch.equal(u, u0) and torch.equal(p, p0)
