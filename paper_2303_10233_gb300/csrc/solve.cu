@@ -717,7 +717,8 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
   if (g->sch->v[S_PEND] != 0.0) { *its = 0; *dstat = g->sch->status; return ETH_OK; }
   int j = 1;
   const bool use_graph = o->graph != 0;
-  const bool device_loop = o->graph == 1;   // 1: the whole loop on the device; 2: host-checked replays
+  // 1: the whole loop on the device; 2 (or a driver without conditional graph nodes): host-checked replays
+  bool device_loop = o->graph == 1 && !w->no_cond_nodes;
   const int key = (int)fp32 * 1000 + (int)(sizeof(T)) * 10 + o->mg_pre + 100 * o->mg_post + 10000 * o->a_exact +
                   20000 * o->mq_mode + 100000 * tile_code(g) + 10000000 * o->graph;
   while (true) {
@@ -741,7 +742,13 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
             body = cp.conditional.phGraph_out[0];
             ge = cudaStreamBeginCaptureToGraph(g->s, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
           }
-          if (ge != cudaSuccess) { cudaGraphDestroy(graph); return cuda_status(ge, "MINRES loop graph"); }
+          if (ge != cudaSuccess) {   // no conditional nodes here: fall back to host-replayed graphs
+            cudaGraphDestroy(graph);
+            cudaGetLastError();
+            w->no_cond_nodes = true;
+            device_loop = false;
+            continue;
+          }
         } else {
           ETH_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
         }

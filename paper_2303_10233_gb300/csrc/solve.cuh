@@ -21,6 +21,7 @@ struct Work {
   cudaGraphExec_t gexec = nullptr;
   int gkey = -1;
   long glaunch = 0;            // kernels in one replay of gexec
+  bool no_cond_nodes = false;  // the driver refused a conditional graph node: host-replayed graphs
   int nmin_built = -1;
   GMRESWork* gm = nullptr;     // GMRES / PCD workspace (Oseen)
   double* pcg = nullptr;       // exact-block inner PCG vectors (4 x 2 N_v + 6 x N_1)
