@@ -128,6 +128,14 @@ def oracle_sample(n, iters, setup=None):
     return info["its"], dt, setup
 
 
+def _config(nt, ws):
+    """The workload both arms run (the reference arm times the oracle on the same one)."""
+    return {"workload": "stokes_mms_256", "n": N_GRID, "N_t": nt, "tol": TOL, "precision": "mixed",
+            "preconditioner": "blkdiag(GMG V(1,1) Jacobi, M_Q^+ via Q1 V-cycle)",
+            "l2": "512 MB buffer written between steps (outside per-step events)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def run_reference(args):
     ws, rank, _ = _dist()
     if rank != 0:
@@ -151,7 +159,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": "stokes_mms_256", "n": N_GRID, "N_t": nt},
+            "data": "synthetic", "config": _config(nt, ws),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -277,10 +285,7 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 applies / f64 Krylov", "data": "synthetic",
-        "config": {"workload": "stokes_mms_256", "n": N_GRID, "N_t": nt, "tol": TOL, "precision": "mixed",
-                   "preconditioner": "blkdiag(GMG V(1,1) Jacobi, M_Q^+ via Q1 V-cycle)",
-                   "l2": "512 MB buffer written between steps (outside per-step events)",
-                   "parallelism": f"replicas x{ws}"},
+        "config": _config(nt, ws),
         "time_to_tol_ms": statistics.median(step_ms),
         "iters_per_solve": its / max(len(stats), 1),
         "relres": max(s["relres_true"] for s in stats),
