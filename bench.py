@@ -29,6 +29,10 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the oracle (CPU baseline / reference arm) is reported as one core: keep its BLAS
+# single-threaded (set before numpy is imported; the GPU path uses no CPU BLAS)
+for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 N_GRID = 256
 SEED = 0
