@@ -934,6 +934,7 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
   ETH_CUDA(cudaStreamSynchronize(g->s));
   const double nb2 = std::sqrt(G->gsh->pcg[0]);
   const double nbred = std::sqrt(std::max(G->gsh->pcg[0] - G->gsh->pcg[1], 0.0));
+  if (!std::isfinite(nb2)) { st->relres_true = nb2; return ETH_ENAN; }   // NaN or Inf in the right-hand side
   if (!(nb2 > 0.0)) { ETH_CUDA(cudaMemsetAsync(w->x, 0, nt * 8, g->s)); st->relres_true = 0; return ETH_OK; }
   const double eta = o->tol;
   int its1 = 0, its2 = 0, s1 = 0, s2 = 0, e1 = 0, e2 = 0;
@@ -971,12 +972,19 @@ eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, b
   // consistent right-hand side (e1 / e0 components removed)
   ETH_CUDA(cudaMemcpyAsync(w->bp, bsrc, (size_t)g->nt * 8, cudaMemcpyDeviceToDevice, g->s));
   ETH_TRY(canonicalize(g, w->bp));
+  double incons = 0.0, nbp = 0.0;
+  ETH_TRY(rhs_inconsistency(g, w, w->bp, &incons, &nbp));
+  eth_status r;
   if (o->precision == ETH_MIXED) {
     ETH_TRY(ensure_hier<float>(g, w, o));
-    return two_stage<float>(g, w, o, st, adjoint, w->bp);
+    r = two_stage<float>(g, w, o, st, adjoint, w->bp);
+  } else {
+    ETH_TRY(ensure_hier<double>(g, w, o));
+    r = two_stage<double>(g, w, o, st, adjoint, w->bp);
   }
-  ETH_TRY(ensure_hier<double>(g, w, o));
-  return two_stage<double>(g, w, o, st, adjoint, w->bp);
+  // the solve used the projected right-hand side; report a removed component as for Stokes
+  if (r == ETH_OK && std::isfinite(nbp) && nbp > 0.0 && incons > 1e-8 * nbp) r = ETH_EINCONSISTENT;
+  return r;
 }
 
 }  // namespace eth

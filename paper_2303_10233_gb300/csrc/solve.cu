@@ -855,6 +855,23 @@ eth_status canonicalize(eth_grid* g, double* x) {
   return ETH_OK;
 }
 
+// After canonicalize(g, bp): the size of the null-space component that was removed,
+// sqrt(s1^2 / n1 + s0^2 / n0) with s1, s0 the removed block sums, and ||bp||.
+eth_status rhs_inconsistency(eth_grid* g, Work* w, const double* bp, double* incons, double* nbp) {
+  const size_t nt = g->nt;
+  const int nb = vblocks(nt);
+  ETH_CUDA(cudaMemsetAsync(w->Kz, 0, nt * 8, g->s));
+  k_residual<<<nb, 256, 0, g->s>>>(nt, bp, w->Kz, w->r, slot_of(g, SL_NORM, nb, FIN_STORE));
+  ETH_CUDA(cudaGetLastError());
+  g->launches++;
+  ETH_CUDA(cudaMemcpyAsync(g->sch->dots, g->sc->dots, sizeof(g->sc->dots), cudaMemcpyDeviceToHost, g->s));
+  ETH_CUDA(cudaStreamSynchronize(g->s));
+  *nbp = std::sqrt(g->sch->dots[SL_NORM]);
+  *incons = std::sqrt(g->sch->dots[SL_PSUM] * g->sch->dots[SL_PSUM] / g->n1 +
+                      g->sch->dots[SL_PSUM + 1] * g->sch->dots[SL_PSUM + 1] / g->n0);
+  return ETH_OK;
+}
+
 template <class T>
 static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, const double* bsrc) {
   const size_t nt = g->nt;
@@ -878,6 +895,10 @@ static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stat
   const double incons = std::sqrt(g->sch->dots[SL_PSUM] * g->sch->dots[SL_PSUM] / g->n1 +
                                   g->sch->dots[SL_PSUM + 1] * g->sch->dots[SL_PSUM + 1] / g->n0);
   eth_status result = ETH_OK;
+  if (!std::isfinite(nb2)) {  // NaN or Inf in the right-hand side: nothing to solve
+    st->relres_true = nb2;
+    return ETH_ENAN;
+  }
   if (nb2 > 0 && incons > 1e-8 * nb2) result = ETH_EINCONSISTENT;
   if (!(nb2 > 0.0)) {  // zero right-hand side: x = 0
     ETH_CUDA(cudaMemsetAsync(w->x, 0, nt * 8, g->s));

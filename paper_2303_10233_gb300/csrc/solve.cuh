@@ -47,6 +47,7 @@ int vblocks(size_t m);
 Slot slot_of(eth_grid* g, int which, int total, int op);
 eth_status read_scalars(eth_grid* g);
 eth_status canonicalize(eth_grid* g, double* x);
+eth_status rhs_inconsistency(eth_grid* g, Work* w, const double* bp, double* incons, double* nbp);
 eth_status true_residual(eth_grid* g, Work* w, const double* b, double* rr, bool trans = false);
 int mq_blocks(eth_grid* g);
 template <class T>

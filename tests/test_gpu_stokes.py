@@ -113,3 +113,32 @@ def test_graph_modes_match_stream_launches(eth, precision):
     for u, p, s in out[1:]:
         assert s["status"] == 0 and s["iters_total"] == s0["iters_total"]
         assert torch.equal(u, u0) and torch.equal(p, p0)
+
+
+@pytest.mark.parametrize("kind", ["stokes", "oseen"])
+def test_failure_statuses(eth, kind):
+    """Failures made on the host, reported as status codes without a device fault:
+    NaN in the body force -> ETH_ENAN; too few iterations -> ETH_ENOTCONV with the
+    reached residual in the statistics; boundary data with a net flux (a right-hand
+    side with a null-space component) -> ETH_EINCONSISTENT."""
+    n = 16
+    w = W.mms(n, seed=2) if kind == "stokes" else W.oseen_cavity(n, nu=1 / 50, seed=2)
+    G = eth.problem(w)
+    _, _, st = G.solve(tol=1e-10, maxit=3)
+    assert st["status"] == 4 and st["relres_true"] > 1e-10
+    f = torch.as_tensor(w["f_nodal"], device="cuda").clone()
+    ub = torch.as_tensor(w["ubc"], device="cuda")
+    f[7] = float("nan")
+    G.set_rhs(f, ub)
+    with pytest.raises(eth.EthError) as ei:
+        G.solve(tol=1e-6, maxit=50)
+    assert ei.value.status == 8
+    g = fem.Grid(n)
+    flux = np.zeros(2 * g.nv)
+    left = np.isclose(g.X2, -1.0) & ~np.isclose(np.abs(g.Y2), 1.0)
+    flux[: g.nv][left] = 1.0                      # inflow through the left side only
+    G.set_rhs(torch.zeros(2 * g.nv, dtype=torch.float64, device="cuda"), torch.as_tensor(flux, device="cuda"))
+    with pytest.raises(eth.EthError) as ei:
+        G.solve(tol=1e-6, maxit=200)
+    assert ei.value.status == 6
+    G.close()
