@@ -165,7 +165,9 @@ eth_status eth_get_rhs(eth_grid* g, double* b_dev);
 
 /* Solves K x = b: Stokes by MINRES (Algorithm 1) with the block-diagonal
  * preconditioner (Eq. stokes_pre), Oseen by the two-stage PCD method
- * (Sec. 3.1).  u_dev (2*N_v) and p_dev (N_1 + N_0) hold the initial guess on
+ * (Sec. 3.1).  The multigrid hierarchies halve n while it stays even, so the
+ * solvers need n = c * 2^k with c <= 32 (ETH_EINVAL otherwise); the operator
+ * applies take any even n.  u_dev (2*N_v) and p_dev (N_1 + N_0) hold the initial guess on
  * entry (boundary entries of u are overwritten by the Dirichlet data) and the
  * solution on exit, with sum(p1) = sum(p0) = 0.  stats may be NULL. */
 eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u_dev,
