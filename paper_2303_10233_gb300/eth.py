@@ -21,6 +21,9 @@ STOKES, OSEEN = 0, 1
 OPS = {"K": 0, "KT": 1, "A": 2, "F": 3, "B": 4, "BT": 5, "MQ": 6, "MV": 7, "K1": 8, "K1T": 9}
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOTCONV", 5: "EBREAKDOWN",
           6: "EINCONSISTENT", 7: "ETIMEOUT", 8: "ENAN"}
+# statuses that still come with a meaningful result (returned, status in the stats):
+# tolerance not reached, and a right-hand side whose null-space component was removed
+SOFT = (0, 4, 6)
 
 
 class EthError(RuntimeError):
@@ -195,7 +198,7 @@ class Grid:
         o = make_opts(**opts)
         st = Stats()
         rc = load().eth_solve(self.h, ctypes.byref(o), _ptr(u), _ptr(p), ctypes.byref(st))
-        if rc not in (0, 4):
+        if rc not in SOFT:
             _check(rc)
         return u, p, st.as_dict()
 
@@ -207,7 +210,7 @@ class Grid:
         st = Stats()
         c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         rc = load().eth_solve_host(self.h, ctypes.byref(o), c(f), c(ub), c(u), c(p), ctypes.byref(st))
-        if rc not in (0, 4):
+        if rc not in SOFT:
             _check(rc)
         return u, p, st.as_dict()
 
@@ -218,7 +221,7 @@ class Grid:
         c = lambda t: ctypes.c_void_p(t.data_ptr())
         rc = load().eth_solve_host(self.h, ctypes.byref(o), c(f_pinned), c(ubc_pinned), c(u_pinned),
                                    c(p_pinned), ctypes.byref(st))
-        if rc not in (0, 4):
+        if rc not in SOFT:
             _check(rc)
         return st.as_dict()
 
@@ -227,7 +230,7 @@ class Grid:
         o = make_opts(**opts)
         st = Stats()
         rc = load().eth_solve_adjoint(self.h, ctypes.byref(o), _ptr(ru), _ptr(rp), _ptr(lu), _ptr(lp), ctypes.byref(st))
-        if rc not in (0, 4):
+        if rc not in SOFT:
             _check(rc)
         return lu, lp, st.as_dict()
 

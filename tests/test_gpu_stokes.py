@@ -120,7 +120,8 @@ def test_failure_statuses(eth, kind):
     """Failures made on the host, reported as status codes without a device fault:
     NaN in the body force -> ETH_ENAN; too few iterations -> ETH_ENOTCONV with the
     reached residual in the statistics; boundary data with a net flux (a right-hand
-    side with a null-space component) -> ETH_EINCONSISTENT."""
+    side with a null-space component) -> ETH_EINCONSISTENT, returned with the solution of
+    the projected system (the binding raises only for the hard failures)."""
     n = 16
     w = W.mms(n, seed=2) if kind == "stokes" else W.oseen_cavity(n, nu=1 / 50, seed=2)
     G = eth.problem(w)
@@ -138,7 +139,6 @@ def test_failure_statuses(eth, kind):
     left = np.isclose(g.X2, -1.0) & ~np.isclose(np.abs(g.Y2), 1.0)
     flux[: g.nv][left] = 1.0                      # inflow through the left side only
     G.set_rhs(torch.zeros(2 * g.nv, dtype=torch.float64, device="cuda"), torch.as_tensor(flux, device="cuda"))
-    with pytest.raises(eth.EthError) as ei:
-        G.solve(tol=1e-6, maxit=200)
-    assert ei.value.status == 6
+    _, _, st = G.solve(tol=1e-6, maxit=400)
+    assert st["status"] == 6   # the projected system is solved; the removal is reported
     G.close()
