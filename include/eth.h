@@ -26,9 +26,11 @@
  * Ownership: the caller owns every pointer argument and never hands it to the
  * library; the handle owns its device workspace (multigrid hierarchy, Krylov
  * basis), allocated at eth_grid_create and freed by eth_grid_destroy.
- * Streams: all device work of a handle is enqueued on the stream given at
- * creation.  eth_apply returns after enqueueing; eth_solve* synchronise that
- * stream once at the end to fill eth_stats.
+ * Streams: device work of a handle is ordered on the stream given at creation:
+ * eth_apply enqueues on it and returns; eth_solve* run on the handle's internal
+ * streams (graphs need a capturable stream), which wait for the work already on
+ * the user stream and are joined back to it, and synchronise once at the end to
+ * fill eth_stats.
  * Errors: every call returns an eth_status; no exception crosses the ABI.
  * eth_last_error() returns a thread-local message for the last failure.
  */
@@ -97,7 +99,9 @@ typedef struct {
                               elements per CTA and the persistent 32 x 8 form
                               (mixed precision) and keep the fastest (cached
                               per grid size, operator and precision for the
-                              process); 0: 32 x 8, one tile per CTA          */
+                              process), and for GMRES the basis vectors per
+                              Gram-Schmidt pass in {4, 8, 16}; 0: 32 x 8, one
+                              tile per CTA, 16 vectors per pass              */
   int restart_max;         /* GMRES: when a restart cycle reduces the FP64
                               residual by less than a factor 2, the next
                               cycles use twice the restart length, up to
