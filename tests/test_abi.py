@@ -41,3 +41,27 @@ def test_create_rejects_bad_sizes_without_device(lib):
     assert lib.eth_set_coefficients(None, 1.0, None) == 1
     assert lib.eth_apply(None, 0, 0, None, None) == 1
     assert lib.eth_status_string(4) == b"not converged"
+
+
+def _header_struct_fields(name):
+    """Field names of `typedef struct { ... } name;` in include/eth.h, in order."""
+    import re
+    src = open(eth.HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        parts = decl.split(None, 1)
+        fields += [f.strip() for f in parts[1].split(",")]
+    return fields
+
+
+@pytest.mark.parametrize("cname,pytype", [("eth_opts", "Opts"), ("eth_stats", "Stats")])
+def test_binding_structs_match_header(cname, pytype):
+    """The ctypes mirrors of eth_opts / eth_stats list the header's fields in order."""
+    ours = [f for f, _ in getattr(eth, pytype)._fields_]
+    assert ours == _header_struct_fields(cname)
