@@ -224,6 +224,21 @@ eth_status eth_adjoint_gradients(eth_grid* g, const double* lu_dev, const double
 eth_status eth_apply_k_dot_static(int n, double x0, double x1, double y0, double y1, double nu, int fp32,
                                   const double* x_dev, double* y_dev, double* dot_dev, void* cuda_stream);
 
+/* Picard iteration for the steady Navier-Stokes problem (Sec. 3: the Oseen
+ * systems are its linearisations).  g must be an ETH_OSEEN grid whose viscosity
+ * was set with eth_set_coefficients (its wind is replaced).  Step 1 solves with
+ * zero wind (the Stokes problem); step k+1 solves the Oseen problem with the
+ * wind w = u_k.  f_nodal_dev, ubc_dev: device, 2*N_v FP64 (as eth_set_rhs).
+ * u_dev, p_dev: device outputs (2*N_v, N_1+N_0), the last iterate.  nlres_host
+ * (steps doubles, may be NULL): after step k the nonlinear residual
+ * ||b(u_k) - K(u_k) [u_k; p_k]|| / ||b(u_k)|| of the system linearised at the
+ * iterate itself (FP64 operator).  stats_host (steps entries, may be NULL): the
+ * statistics of each Oseen solve.  Returns the first hard failure of a solve
+ * (ETH_ENOTCONV of a step does not stop the iteration).  On return the grid's
+ * coefficients and right-hand side are those linearised at the last iterate. */
+eth_status eth_picard(eth_grid* g, const eth_opts* opts, const double* f_nodal_dev, const double* ubc_dev,
+                      int steps, double* u_dev, double* p_dev, double* nlres_host, eth_stats* stats_host);
+
 /* Batched solves of independent instances (each created with its own handle,
  * all on the same stream). */
 eth_status eth_batch_create(int count, eth_grid* const* grids, eth_batch** out);

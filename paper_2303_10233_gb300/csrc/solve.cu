@@ -1132,4 +1132,50 @@ eth_status eth_batch_solve(eth_batch* b, const eth_opts* opts, double* const* u,
 }
 
 void eth_batch_destroy(eth_batch* b) { delete b; }
+
+// Picard iteration for steady Navier-Stokes (Sec. 3): each step is an Oseen solve
+// whose wind is the previous velocity (zero wind first, i.e. the Stokes problem).
+// After each step the coefficients are set to the new velocity, so the next step's
+// system is in place, and the nonlinear residual ||b(u) - K(u)[u; p]|| / ||b(u)||
+// is evaluated with FP64 element arithmetic.
+eth_status eth_picard(eth_grid* g, const eth_opts* opts, const double* f_nodal, const double* ubc, int steps,
+                      double* u, double* p, double* nlres, eth_stats* stats) {
+  if (!g || !f_nodal || !ubc || !u || !p) { set_error("eth_picard: NULL argument"); return ETH_EINVAL; }
+  if (g->kind != ETH_OSEEN) { set_error("eth_picard: the grid must be created as ETH_OSEEN"); return ETH_EINVAL; }
+  if (!g->has_coef) { set_error("eth_picard: call eth_set_coefficients first (viscosity)"); return ETH_EINVAL; }
+  if (steps < 1) { set_error("eth_picard: steps=%d must be >= 1", steps); return ETH_EINVAL; }
+  const size_t nu2 = 2 * (size_t)g->nv, np = (size_t)g->n1 + g->n0, nt = g->nt;
+  const double nu = g->nu;
+  ETH_CUDA(cudaMemsetAsync(u, 0, nu2 * 8, g->s));
+  ETH_CUDA(cudaMemsetAsync(p, 0, np * 8, g->s));
+  ETH_CUDA(cudaMemsetAsync(g->tmp, 0, nu2 * 8, g->s));   // zero wind of the first step
+  ETH_TRY(eth_set_coefficients(g, nu, g->tmp));
+  ETH_TRY(eth_set_rhs(g, f_nodal, ubc));
+  Work* w;
+  ETH_TRY(work_get(g, &w));
+  for (int k = 0; k < steps; ++k) {
+    eth_stats st;
+    std::memset(&st, 0, sizeof(st));
+    const eth_status r = eth_solve(g, opts, u, p, &st);
+    if (stats) stats[k] = st;
+    if (r != ETH_OK && r != ETH_ENOTCONV && r != ETH_EINCONSISTENT) return r;
+    // linearise at the new iterate (this is also the next step's system) and measure it there
+    ETH_TRY(eth_set_coefficients(g, nu, u));
+    ETH_TRY(eth_set_rhs(g, f_nodal, ubc));
+    if (nlres) {
+      ETH_CUDA(cudaMemcpyAsync(g->tmp, u, nu2 * 8, cudaMemcpyDeviceToDevice, g->s));
+      ETH_CUDA(cudaMemcpyAsync(g->tmp + nu2, p, np * 8, cudaMemcpyDeviceToDevice, g->s));
+      ETH_TRY(op_apply(g, ETH_OP_K, false, g->tmp, g->tmp2));
+      double incons = 0.0, nb = 0.0;
+      ETH_TRY(rhs_inconsistency(g, w, g->b, &incons, &nb));
+      const int nbk = vblocks(nt);
+      k_residual<<<nbk, 256, 0, g->s>>>(nt, g->b, g->tmp2, w->r, slot_of(g, SL_NORM, nbk, FIN_STORE));
+      ETH_CUDA(cudaGetLastError());
+      ETH_CUDA(cudaMemcpyAsync(&g->sch->dots[SL_NORM], &g->sc->dots[SL_NORM], 8, cudaMemcpyDeviceToHost, g->s));
+      ETH_CUDA(cudaStreamSynchronize(g->s));
+      nlres[k] = nb > 0.0 ? std::sqrt(g->sch->dots[SL_NORM]) / nb : 0.0;
+    }
+  }
+  return ETH_OK;
+}
 }

@@ -82,6 +82,7 @@ def load(path=LIB_PATH):
         "eth_solve": (i, [vp, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]),
         "eth_solve_host": (i, [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Stats)]),
         "eth_solve_adjoint": (i, [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Stats)]),
+        "eth_picard": (i, [vp, ctypes.POINTER(Opts), vp, vp, i, vp, vp, ctypes.POINTER(d), ctypes.POINTER(Stats)]),
         "eth_apply": (i, [vp, i, i, vp, vp]),
         "eth_adjoint_gradients": (i, [vp, vp, vp, vp, ctypes.POINTER(d)]),
         "eth_apply_k_dot_static": (i, [i, d, d, d, d, d, i, vp, vp, vp, vp]),
@@ -234,6 +235,19 @@ class Grid:
             _check(rc)
         return lu, lp, st.as_dict()
 
+
+    def picard(self, f_nodal, ubc, steps, **opts):
+        """Picard iteration for steady Navier-Stokes (Oseen grid; zero wind first).
+        Returns (u, p, nonlinear residual per step, stats per step)."""
+        u = self._zeros(2 * self.nv); p = self._zeros(self.n1 + self.n0)
+        o = make_opts(**opts)
+        res = (ctypes.c_double * steps)()
+        st = (Stats * steps)()
+        rc = load().eth_picard(self.h, ctypes.byref(o), _ptr(f_nodal), _ptr(ubc), int(steps), _ptr(u), _ptr(p),
+                               res, st)
+        if rc not in SOFT:
+            _check(rc)
+        return u, p, list(res), [s_.as_dict() for s_ in st]
 
     def adjoint_gradients(self, lu, u):
         """(grad_f, grad_nu) of J = ||u - u_t||^2 from the adjoint velocity lu."""

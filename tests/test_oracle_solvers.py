@@ -132,3 +132,25 @@ def test_batch_workload_totals():
     assert 5e6 < tot < 30e6
     assert all(i["wind"] is None for i in insts[0::2])
     assert all(i["wind"] is not None for i in insts[1::2])
+
+
+def test_picard_pins():
+    """Picard iteration (Sec. 3): the first step with zero wind is the Stokes solution;
+    at a low Reynolds number the iteration contracts, its nonlinear residual falls
+    monotonically to roundoff, and the limit satisfies the discrete Navier-Stokes
+    equations K(u) x = b(u) with the wind equal to its own velocity."""
+    from oracle import picard
+    from paper_2303_10233_gb300 import workloads as W
+    n = 8
+    w = W.cavity(n, nu=0.2)
+    g = fem.Grid(n)
+    xs, res = picard.picard(g, w["nu"], w["f_nodal"], w["ubc"], 14)
+    s0 = problem.System(g, w["nu"])
+    xst, _ = direct.solve(s0, s0.rhs(w["f_nodal"], w["ubc"]))
+    assert np.linalg.norm(xs[0] - xst) <= 1e-12 * np.linalg.norm(xst)
+    assert all(b < a for a, b in zip(res[:10], res[1:11]))
+    assert res[-1] <= 1e-11 < res[0]
+    # at the limit, one more Oseen solve with the limit's own wind reproduces it
+    s = problem.System(g, w["nu"], xs[-1][: g.nu].copy())
+    x1, _ = direct.solve(s, s.rhs(w["f_nodal"], w["ubc"]))
+    assert np.linalg.norm(s.canonical(x1) - xs[-1]) <= 1e-9 * np.linalg.norm(xs[-1])
