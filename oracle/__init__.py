@@ -25,6 +25,7 @@ two-level pressure approximation"):
 * ``adjoint``  -- adjoint solve and gradients w.r.t. body force and viscosity.
 * ``rows``     -- selected entries of K x element by element (no assembly), for
                   sampled parity at full grid sizes.
+* ``picard``   -- Picard iteration for steady Navier-Stokes with direct Oseen solves.
 
 Parity pins live in ``tests/test_oracle_*.py``.  Functions with no pin say
 "parity unpinned" in their docstring.
