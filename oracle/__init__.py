@@ -26,6 +26,8 @@ two-level pressure approximation"):
 * ``rows``     -- selected entries of K x element by element (no assembly), for
                   sampled parity at full grid sizes.
 * ``picard``   -- Picard iteration for steady Navier-Stokes with direct Oseen solves.
+* ``infsup``   -- the discrete inf-sup constant gamma^2 (dense pencil, Sec. 2.4) and
+                  its EST-MINRES estimate from the Lanczos scalars of MINRES.
 
 Parity pins live in ``tests/test_oracle_*.py``.  Functions with no pin say
 "parity unpinned" in their docstring.

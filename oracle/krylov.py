@@ -42,7 +42,11 @@ def minres(K, Pinv, b, x0, tol=1e-8, maxit=1000, true_tol=None):
     i.e. the P^{-1}-norm of the residual is reduced by ``tol`` (Sec. 2.4), or,
     when ``true_tol`` is given, additionally requires the Euclidean residual
     ||b - K x|| <= true_tol * ||b|| (checked when the eta test first passes).
-    Returns (x, info) with info["its"], info["eta"] (history of |eta|).
+    Returns (x, info) with info["its"], info["eta"] (history of |eta|) and the
+    coefficients of the preconditioned Lanczos process the recurrence runs on:
+    info["delta"] = [delta_1 .. delta_k] (diagonal of T_k) and info["gamma"] =
+    [gamma_1 .. gamma_{k+1}] (gamma_2 .. gamma_k off the diagonal of T_k,
+    gamma_{k+1} the entry below it in T_{k+1,k}).
     """
     x = np.array(x0, dtype=np.float64, copy=True)
     v_old = np.zeros_like(x)                    # v^(j-1), starts as v^(0) = 0
@@ -56,11 +60,12 @@ def minres(K, Pinv, b, x0, tol=1e-8, maxit=1000, true_tol=None):
     s_old = s = 0.0                             # s_0, s_1
     c_old = c = 1.0                             # c_0, c_1
     hist = [abs(eta)]
+    deltas, gammas = [], [gamma]
     eta1 = abs(eta)
     bnorm = np.linalg.norm(b)
     its = 0
     if eta1 == 0.0:
-        return x, {"its": 0, "eta": hist}
+        return x, {"its": 0, "eta": hist, "delta": deltas, "gamma": gammas}
     for j in range(1, maxit + 1):
         z = z / gamma
         Kz = K(z)
@@ -70,6 +75,8 @@ def minres(K, Pinv, b, x0, tol=1e-8, maxit=1000, true_tol=None):
             v_new -= (gamma / gamma_old) * v_old
         z_new = Pinv(v_new)
         gamma_new = np.sqrt(np.dot(z_new, v_new))
+        deltas.append(delta)
+        gammas.append(gamma_new)
         a0 = c * delta - c_old * s * gamma
         a1 = np.sqrt(a0 * a0 + gamma_new * gamma_new)
         a2 = s * delta + c_old * c * gamma
@@ -93,7 +100,7 @@ def minres(K, Pinv, b, x0, tol=1e-8, maxit=1000, true_tol=None):
                 break
         if gamma == 0.0:
             break
-    return x, {"its": its, "eta": hist}
+    return x, {"its": its, "eta": hist, "delta": deltas, "gamma": gammas}
 
 
 # ---------------------------------------------------------------------------
