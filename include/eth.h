@@ -239,6 +239,31 @@ eth_status eth_apply_k_dot_static(int n, double x0, double x1, double y0, double
 eth_status eth_picard(eth_grid* g, const eth_opts* opts, const double* f_nodal_dev, const double* ubc_dev,
                       int steps, double* u_dev, double* p_dev, double* nlres_host, eth_stats* stats_host);
 
+/* Capacity of the Lanczos record of a Stokes solve (iterations of its first MINRES run). */
+#define ETH_LANCZOS_CAP 4096
+
+/* Lanczos coefficients of the first MINRES run of the last Stokes solve on g
+ * (Algorithm 1 runs a Lanczos process on P^{-1} K): delta_dev[j-1] = delta_j
+ * (the diagonal of T_j) and gamma_dev[j-1] = gamma_{j+1} (the entry below it),
+ * j = 1 .. min(k, cap), copied into device arrays of cap FP64 (either may be
+ * NULL when cap is 0).  *k_host receives the number of recorded iterations (at
+ * most ETH_LANCZOS_CAP; 0 before any Stokes solve).  With mixed precision and
+ * iterative refinement only the first (longest) MINRES run is recorded.
+ * Synchronises g's stream.  ETH_EINVAL for an Oseen grid or NULL pointers. */
+eth_status eth_lanczos(eth_grid* g, int cap, double* delta_dev, double* gamma_dev, int* k_host);
+
+/* EST-MINRES estimates of the discrete inf-sup constant gamma^2 (Sec. 2.4: the
+ * smallest nonzero eigenvalue of B A^{-1} B^T v = lambda M_Q v, v orthogonal to
+ * k).  From k Lanczos steps (device arrays in the layout of eth_lanczos) writes
+ * est_dev[j-1] = theta^2 - theta for each j = 1 .. k, theta the negative
+ * harmonic Ritz value of T_j closest to zero, or NaN while T_j has none (or is
+ * singular).  With the exact block preconditioner P_1 (opts a_exact = 1, mq_mode
+ * = ETH_MQ_EXACT) the estimates approach gamma^2 from above; with approximate
+ * blocks they estimate the corresponding quantity of that preconditioner.
+ * Asynchronous on g's stream; g only supplies the stream.  One device thread
+ * per j, each O(j) work per bisection step. */
+eth_status eth_est_infsup(eth_grid* g, const double* delta_dev, const double* gamma_dev, int k, double* est_dev);
+
 /* Batched solves of independent instances (each created with its own handle,
  * all on the same stream). */
 eth_status eth_batch_create(int count, eth_grid* const* grids, eth_batch** out);

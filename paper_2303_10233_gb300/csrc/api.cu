@@ -103,6 +103,7 @@ eth_status eth_grid_create(int n, double x0, double x1, double y0, double y1, et
   A((void**)&g->sc, sizeof(Scalars));
   A((void**)&g->part, (size_t)16 * g->part_cap * 8);
   A((void**)&g->ticket, 16 * sizeof(unsigned));
+  A((void**)&g->lz, 2 * (size_t)ETH_LANCZOS_CAP * 8);
   if (kind == ETH_OSEEN) { A((void**)&g->wind, nu2 * 8); A((void**)&g->windf, nu2 * 4); }
   if (e == cudaSuccess) e = cudaMallocHost((void**)&g->sch, sizeof(Scalars));
   if (e == cudaSuccess) e = cudaMemsetAsync(g->ticket, 0, 16 * sizeof(unsigned), g->s);
@@ -122,7 +123,7 @@ void eth_grid_destroy(eth_grid* g) {
   if (g->s) cudaStreamSynchronize(g->s); else cudaDeviceSynchronize();
   solver_free(g);
   cudaFree(g->b); cudaFree(g->ubc); cudaFree(g->tmp); cudaFree(g->tmp2);
-  cudaFree(g->sc); cudaFree(g->part); cudaFree(g->ticket);
+  cudaFree(g->sc); cudaFree(g->part); cudaFree(g->ticket); cudaFree(g->lz);
   cudaFree(g->wind); cudaFree(g->windf);
   if (g->sch) cudaFreeHost(g->sch);
   delete g;

@@ -58,6 +58,7 @@ struct eth_grid {
   double* part = nullptr;     // reduction partials
   unsigned* ticket = nullptr; // reduction tickets (16)
   int part_cap = 0;
+  double* lz = nullptr;       // Lanczos coefficients of MINRES (2 x ETH_LANCZOS_CAP)
   // solver workspaces are created lazily by the solvers
   void* ws = nullptr;
   void (*ws_free)(void*) = nullptr;

@@ -16,6 +16,11 @@ struct Scalars {
   int inner_done;        // unused
   int idone[4];          // early-exit flags of inner (nested) PCG solves
   int loops, max_loops;  // bodies run by the device-side MINRES loop and their cap
+  // Lanczos coefficients of the first MINRES run of a Stokes solve (EST-MINRES,
+  // Sec. 2.4): lz_delta[j-1] = delta_j, lz_gamma[j-1] = gamma_{j+1}, j = 1 .. lz_n.
+  double* lz_delta;
+  double* lz_gamma;
+  int lz_cap, lz_runs, lz_n;
 };
 
 // Inner PCG state blocks (exact preconditioner blocks): base index of each.
@@ -63,6 +68,11 @@ __device__ __forceinline__ void finish_minres_gamma(Scalars* sc, double g2) {
     g2 = 0.0;
   }
   const double gnew = sqrt(g2);
+  if (sc->lz_runs == 1 && sc->lz_n < sc->lz_cap) {
+    sc->lz_delta[sc->lz_n] = v[S_DELTA];
+    sc->lz_gamma[sc->lz_n] = gnew;
+    sc->lz_n += 1;
+  }
   const double gj = v[S_G], delta = v[S_DELTA];
   const double a0 = v[S_C] * delta - v[S_CPREV] * v[S_S] * gj;
   const double a1 = sqrt(a0 * a0 + gnew * gnew);

@@ -204,6 +204,8 @@ __global__ void k_minres_loop(cudaGraphConditionalHandle h, Scalars* sc) {
 
 __global__ void k_init_scalars(Scalars* sc, double tol, double n1, double n0, double mqc, double nu, int maxit) {
   ETH_GRID_DEP_WAIT();
+  sc->lz_runs += 1;             // Lanczos coefficients are kept for the first run only
+  if (sc->lz_runs == 1) sc->lz_n = 0;
   sc->loops = 0;
   sc->max_loops = (maxit + 1) / 2;   // two MINRES iterations per loop body
   for (int k = 0; k < S_LAST; ++k) sc->v[k] = 0.0;
@@ -425,11 +427,20 @@ __global__ void k_dot1(size_t m, const double* __restrict__ a, const double* __r
   if (slot_arrive<1>(sl, blockIdx.x, v)) finish_slot(sl, v[0]);
 }
 
+// Level-0 right-hand side b = a of the Q1 V-cycle and its first Jacobi step from
+// zero, x = omega D^{-1} b, which vcycle_q1_from expects in place: without it
+// level 0 would start from the previous call's iterate and the V-cycle would not
+// be a linear (let alone symmetric) preconditioner.
 template <class T>
-__global__ void k_to_t(int m, const double* __restrict__ a, T* __restrict__ b, const int* done) {
+__global__ void k_to_t(int m, const double* __restrict__ a, T omega, const T* __restrict__ dinv, T* __restrict__ b,
+                       T* __restrict__ x, const int* done) {
   ETH_GRID_DEP_WAIT();
   if (*done) return;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) b[k] = cvt<T, double>(a[k]);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const T v = cvt<T, double>(a[k]);
+    b[k] = v;
+    x[k] = omega * dinv[k] * v;
+  }
 }
 template <class T>
 __global__ void k_from_t(int m, const T* __restrict__ a, double* __restrict__ b, const int* done) {
@@ -529,7 +540,7 @@ static eth_status schur_pcg(eth_grid* g, Work* w, const eth_opts* o, const doubl
   const cudaStream_t keep = g->s;
   g->s = s;
   auto precond = [&](const double* rr, double* zz) -> eth_status {
-    k_to_t<T><<<nb, 256, 0, s>>>(m, rr, Q.lv[0].b, idone);
+    k_to_t<T><<<nb, 256, 0, s>>>(m, rr, (T)Q.omega, Q.lv[0].dinv, Q.lv[0].b, Q.lv[0].x, idone);
     ETH_CUDA(cudaGetLastError());
     const T* res = nullptr;
     ETH_TRY(vcycle_q1_from<T>(g, Q, 1, 1, idone, &res));
@@ -872,10 +883,23 @@ eth_status rhs_inconsistency(eth_grid* g, Work* w, const double* bp, double* inc
   return ETH_OK;
 }
 
+// Attaches the grid's Lanczos buffers to its scalars and restarts the recording.
+__global__ void k_lz_begin(Scalars* sc, double* lz, int cap) {
+  ETH_GRID_DEP_WAIT();
+  sc->lz_delta = lz;
+  sc->lz_gamma = lz + cap;
+  sc->lz_cap = cap;
+  sc->lz_runs = 0;
+  sc->lz_n = 0;
+}
+
 template <class T>
 static eth_status stokes_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, const double* bsrc) {
   const size_t nt = g->nt;
   const bool fp32 = o->precision == ETH_MIXED;
+  k_lz_begin<<<1, 1, 0, g->s>>>(g->sc, g->lz, ETH_LANCZOS_CAP);
+  ETH_CUDA(cudaGetLastError());
+  g->launches++;
   // consistent right-hand side: b with its e1 / e0 components removed
   ETH_CUDA(cudaMemcpyAsync(w->bp, bsrc, nt * 8, cudaMemcpyDeviceToDevice, g->s));
   ETH_TRY(canonicalize(g, w->bp));

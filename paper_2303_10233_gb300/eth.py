@@ -84,6 +84,8 @@ def load(path=LIB_PATH):
         "eth_solve_adjoint": (i, [vp, ctypes.POINTER(Opts), vp, vp, vp, vp, ctypes.POINTER(Stats)]),
         "eth_picard": (i, [vp, ctypes.POINTER(Opts), vp, vp, i, vp, vp, ctypes.POINTER(d), ctypes.POINTER(Stats)]),
         "eth_apply": (i, [vp, i, i, vp, vp]),
+        "eth_lanczos": (i, [vp, i, vp, vp, pi]),
+        "eth_est_infsup": (i, [vp, vp, vp, i, vp]),
         "eth_adjoint_gradients": (i, [vp, vp, vp, vp, ctypes.POINTER(d)]),
         "eth_apply_k_dot_static": (i, [i, d, d, d, d, d, i, vp, vp, vp, vp]),
         "eth_batch_create": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
@@ -248,6 +250,25 @@ class Grid:
         if rc not in SOFT:
             _check(rc)
         return u, p, list(res), [s_.as_dict() for s_ in st]
+
+    def lanczos(self):
+        """(delta, gamma) of the first MINRES run of the last Stokes solve: delta[j-1] =
+        delta_j, gamma[j-1] = gamma_{j+1} (FP64 device tensors)."""
+        import torch
+        k = ctypes.c_int()
+        _check(load().eth_lanczos(self.h, 0, None, None, ctypes.byref(k)))
+        d = torch.empty(k.value, dtype=torch.float64, device=self.device)
+        gm = torch.empty(k.value, dtype=torch.float64, device=self.device)
+        _check(load().eth_lanczos(self.h, k.value, _ptr(d), _ptr(gm), ctypes.byref(k)))
+        return d, gm
+
+    def est_infsup(self, delta=None, gamma=None):
+        """EST-MINRES estimates of gamma^2 after each MINRES iteration (NaN where none)."""
+        if delta is None:
+            delta, gamma = self.lanczos()
+        est = self._zeros(delta.numel())
+        _check(load().eth_est_infsup(self.h, _ptr(delta), _ptr(gamma), int(delta.numel()), _ptr(est)))
+        return est
 
     def adjoint_gradients(self, lu, u):
         """(grad_f, grad_nu) of J = ||u - u_t||^2 from the adjoint velocity lu."""

@@ -21,6 +21,8 @@ Workloads (all on [-1, 1]^2):
                      nodal speed.
 * ``batch``       -- 64 mixed Stokes/Oseen instances of uneven size and viscosity.
 * ``diff``        -- the differentiation problem (Oseen 256^2, nu = 1/200).
+* ``tridiagonal`` -- random symmetric tridiagonal coefficients (diagonal and
+                     positive off-diagonal), the shape of a Lanczos record.
 """
 from __future__ import annotations
 
@@ -189,3 +191,11 @@ def diff(n=256, nu=1.0 / 200.0):
     w["f_nodal"] = f["u_exact"].copy()
     w["u_target"] = mms(n, seed=5)["u_exact"].copy()
     return w
+
+
+def tridiagonal(k, seed=0):
+    """(delta, gamma): k diagonal entries uniform on [-1, 2] and k off-diagonal
+    entries uniform on [0.05, 1] (gamma[j-1] couples rows j and j+1; the last one
+    sits below a k x k block)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 2.0, k), rng.uniform(0.05, 1.0, k)
