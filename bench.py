@@ -396,6 +396,41 @@ def profile_solve(n, kind):
     G.close()
 
 
+def est_table(nmax):
+    """EST-MINRES inf-sup estimates on the lid-driven cavity for n = 16, 32, .., nmax
+    (one JSON line per grid): MINRES iterations and the final gamma^2 estimate with
+    the exact blocks of P_1 (FP64, inner CG to 1e-12) and with the default
+    multigrid approximations (mixed precision, first refinement pass), the solve
+    time and the CUDA-event time of the estimate kernel (all iterations' estimates)."""
+    import __graft_entry__ as ge
+    ge.build()
+    import torch
+    from paper_2303_10233_gb300 import eth, workloads as W
+    n = 16
+    while n <= nmax:
+        w = W.cavity(n)
+        row = {"n": n}
+        for tag, opts in (("p1", dict(precision="fp64", a_exact=1, mq_mode=1, inner_tol=1e-12)),
+                          ("mg", dict(precision="mixed"))):
+            G = eth.problem(w)
+            _, _, st = G.solve(tol=1e-8, **opts)
+            d, gm = G.lanczos()
+            est = G.est_infsup(d, gm)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(G.stream):
+                e0.record()
+                for _ in range(20):
+                    G.est_infsup(d, gm)
+                e1.record()
+            e1.synchronize()
+            row[tag] = {"its": st["iters_total"], "lanczos_steps": int(d.numel()),
+                        "gamma2_est": float(est[-1].item()), "solve_ms": round(st["seconds"] * 1e3, 2),
+                        "est_us": round(e0.elapsed_time(e1) / 20 * 1e3, 1)}
+            G.close()
+        print(json.dumps(row))
+        n *= 2
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -408,7 +443,12 @@ def main():
     ap.add_argument("--profile-kind", default="stokes", choices=["stokes", "oseen"])
     ap.add_argument("--profile-solve", type=int, default=0, metavar="N",
                     help="only run two default solves on an N x N grid of --profile-kind (for ncu launch lists)")
+    ap.add_argument("--est", type=int, default=0, metavar="N",
+                    help="only print EST-MINRES inf-sup estimates on cavity grids 16 .. N")
     args = ap.parse_args()
+    if args.est:
+        est_table(args.est)
+        return
     if args.profile_apply:
         profile_apply(args.profile_apply, args.profile_kind)
         return
