@@ -26,6 +26,8 @@ two-level pressure approximation"):
 * ``rows``     -- selected entries of K x element by element (no assembly), for
                   sampled parity at full grid sizes.
 * ``picard``   -- Picard iteration for steady Navier-Stokes with direct Oseen solves.
+* ``lsc``      -- least-squares commutator approximation M_S of the Schur complement for
+                  the two-field pressure and the block-triangular M_3 (Sec. 3.2).
 * ``infsup``   -- the discrete inf-sup constant gamma^2 (dense pencil, Sec. 2.4) and
                   its EST-MINRES estimate from the Lanczos scalars of MINRES.
 
