@@ -28,6 +28,8 @@ two-level pressure approximation"):
 * ``picard``   -- Picard iteration for steady Navier-Stokes with direct Oseen solves.
 * ``lsc``      -- least-squares commutator approximation M_S of the Schur complement for
                   the two-field pressure and the block-triangular M_3 (Sec. 3.2).
+* ``step``     -- inflow-outflow flow on a masked uniform grid (the flow over a step,
+                  Sec. 3 Test problem 3): natural outflow, null space [0; k] only.
 * ``infsup``   -- the discrete inf-sup constant gamma^2 (dense pencil, Sec. 2.4) and
                   its EST-MINRES estimate from the Lanczos scalars of MINRES.
 

@@ -1,0 +1,210 @@
+"""Inflow-outflow flow on a masked uniform grid: the flow over a step (test
+infrastructure only).
+
+Sec. 3, Test problem 3: D = [-1, 0) x [0, 1]  U  [0, 5] x [-1, 1], viscosity 1/50,
+parabolic inflow u = (4y(1 - y), 0) at x = -1, the natural (do-nothing) condition
+at the outflow x = 5, no-slip walls elsewhere; the Oseen system is the one after
+five Picard steps from the Stokes solution.  The grid is uniform with square
+elements of side h on the bounding box [-1, 5] x [-1, 1]; an element is active
+when it lies in D.
+
+Layout.  Unknowns live on the full lattice of the bounding box (Q2 nodes, Q1
+nodes, P0 elements), ordered as on the square grid; those of inactive nodes or
+elements are kept with identity rows and value 0.  Velocity rows are identity at
+Dirichlet nodes: active nodes on the boundary of D except those strictly inside
+the outflow edge (the outflow corners belong to the walls).  The natural outflow
+condition needs nothing else: it is what the weak form gives where no Dirichlet
+row is imposed.
+
+Null space.  The frame vector k (1 on the active Q1 nodes, -1 on the active
+elements) is the zero function, so B^T k = 0 and M_Q k = 0 whatever the boundary
+conditions; with an outflow boundary the constant pressure is no longer in
+ker B^T, so the system is singular along [0; k] only (Sec. 2, one-dimensional
+pressure null space).  Solutions are returned with k^T p = 0.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import direct, fem
+
+
+class MaskedGrid:
+    """nx x ny square elements of side h from (x0, y0); ``active`` is (ny, nx) bool.
+    ``x_out``: abscissa of the outflow edge (natural condition), or None."""
+
+    tables = fem.Grid.tables
+
+    def __init__(self, nx, ny, h, x0, y0, active, x_out=None):
+        self.nx, self.ny = int(nx), int(ny)
+        self.hx = self.hy = float(h)
+        self.x0, self.y0 = float(x0), float(y0)
+        self.Nx, self.Ny = 2 * self.nx + 1, 2 * self.ny + 1
+        self.nv = self.Nx * self.Ny
+        self.nu = 2 * self.nv
+        self.n1 = (self.nx + 1) * (self.ny + 1)
+        self.n0 = self.nx * self.ny
+        self.np_ = self.n1 + self.n0
+        self.nt = self.nu + self.np_
+        act = np.asarray(active, dtype=bool).reshape(self.ny, self.nx)
+        self.active = act
+        self.elems = np.flatnonzero(act.ravel())           # element e = ey*nx + ex
+        ex, ey = self.elems % self.nx, self.elems // self.nx
+        a = np.array([0, 1, 2, 0, 1, 2, 0, 1, 2]); b = np.array([0, 0, 0, 1, 1, 1, 2, 2, 2])
+        self.q2_conn = (2 * ey[:, None] + b[None, :]) * self.Nx + (2 * ex[:, None] + a[None, :])
+        c = np.array([0, 1, 0, 1]); d = np.array([0, 0, 1, 1])
+        self.q1_conn = (ey[:, None] + d[None, :]) * (self.nx + 1) + (ex[:, None] + c[None, :])
+        self.q2_active = np.zeros(self.nv, dtype=bool); self.q2_active[self.q2_conn.ravel()] = True
+        self.q1_active = np.zeros(self.n1, dtype=bool); self.q1_active[self.q1_conn.ravel()] = True
+        self.p0_active = act.ravel().copy()
+        jj, ii = np.divmod(np.arange(self.nv), self.Nx)
+        self.X2 = self.x0 + 0.5 * h * ii
+        self.Y2 = self.y0 + 0.5 * h * jj
+        # a node is interior when every element slot around it is an active element
+        inner = np.ones(self.nv, dtype=bool)
+        for node in range(self.nv):
+            i, j = ii[node], jj[node]
+            exs = [i // 2 - 1, i // 2] if i % 2 == 0 else [i // 2]
+            eys = [j // 2 - 1, j // 2] if j % 2 == 0 else [j // 2]
+            for e_y in eys:
+                for e_x in exs:
+                    if not (0 <= e_x < self.nx and 0 <= e_y < self.ny and act[e_y, e_x]):
+                        inner[node] = False
+        bnd = self.q2_active & ~inner
+        self.outflow = np.zeros(self.nv, dtype=bool)
+        if x_out is not None:
+            on = bnd & np.isclose(self.X2, x_out)
+            ys = self.Y2[on]
+            # strictly inside the outflow edge: not at its two wall corners
+            self.outflow = on & (self.Y2 > ys.min() + 1e-12) & (self.Y2 < ys.max() - 1e-12)
+        self.dirichlet = bnd & ~self.outflow
+        self.fixed = self.dirichlet | ~self.q2_active      # identity velocity rows
+        self.bnd = self.fixed                               # same role as Grid.bnd
+
+
+def step_grid(m):
+    """The step domain with h = 1/m (nx = 6m, ny = 2m)."""
+    nx, ny = 6 * m, 2 * m
+    h = 1.0 / m
+    xc = -1.0 + h * (np.arange(nx) + 0.5)
+    yc = -1.0 + h * (np.arange(ny) + 0.5)
+    X, Y = np.meshgrid(xc, yc, indexing="xy")
+    active = ~((X < 0.0) & (Y < 0.0))
+    return MaskedGrid(nx, ny, h, -1.0, -1.0, active, x_out=5.0)
+
+
+def channel_grid(m, length=2.0):
+    """The channel [0, length] x [-1, 1] with h = 1/m and outflow at x = length."""
+    nx, ny = int(round(length * m)), 2 * m
+    return MaskedGrid(nx, ny, 1.0 / m, 0.0, -1.0, np.ones((ny, nx), dtype=bool), x_out=length)
+
+
+class StepSystem:
+    """Assembled FP64 Stokes (wind None) or Oseen system on a MaskedGrid."""
+
+    def __init__(self, g: MaskedGrid, nu, wind=None):
+        self.g = g
+        self.nu = float(nu)
+        E = fem.element_matrices(g)
+        nv, n1, n0 = g.nv, g.n1, g.n0
+        A = fem._assemble(g.q2_conn, g.q2_conn, E["A"], (nv, nv))
+        self.Mv = fem._assemble(g.q2_conn, g.q2_conn, E["M2"], (nv, nv))
+        Fs = self.nu * A
+        if wind is not None:
+            Fs = Fs + fem.convection_q2(g, np.asarray(wind, dtype=np.float64))
+        self.Fs = Fs.tocsr()
+        e = g.elems[:, None]
+        B1 = sp.hstack([fem._assemble(g.q1_conn, g.q2_conn, E["B1x"], (n1, nv)),
+                        fem._assemble(g.q1_conn, g.q2_conn, E["B1y"], (n1, nv))])
+        B0 = sp.hstack([fem._assemble(e, g.q2_conn, E["B0x"], (n0, nv)),
+                        fem._assemble(e, g.q2_conn, E["B0y"], (n0, nv))])
+        self.B = sp.vstack([B1, B0]).tocsr()
+        Qk = fem._assemble(g.q1_conn, g.q1_conn, E["Qk"], (n1, n1))
+        R = fem._assemble(e, g.q1_conn, E["R"], (n0, n1))
+        Q0 = sp.diags(E["Q0"][0, 0] * g.p0_active.astype(float))
+        self.MQ = sp.bmat([[Qk, R.T], [R, Q0]]).tocsr()
+        di = (~g.fixed).astype(float)
+        self.DIs, self.DBs = sp.diags(di), sp.diags(1.0 - di)
+        self.DI = sp.block_diag([self.DIs, self.DIs]).tocsr()
+        self.DB = sp.block_diag([self.DBs, self.DBs]).tocsr()
+        FsI = (self.DIs @ self.Fs @ self.DIs + self.DBs).tocsr()
+        self.F = sp.block_diag([FsI, FsI]).tocsr()
+        AsI = (self.DIs @ (self.nu * A) @ self.DIs + self.DBs).tocsr()
+        self.Anu = sp.block_diag([AsI, AsI]).tocsr()
+        self.BI = (self.B @ self.DI).tocsr()
+        pin = np.concatenate([~g.q1_active, ~g.p0_active]).astype(float)
+        self.K = sp.bmat([[self.F, self.BI.T], [self.BI, sp.diags(pin)]]).tocsr()
+        self.k = np.concatenate([g.q1_active.astype(float), -g.p0_active.astype(float)])
+        self.kx = np.concatenate([np.zeros(g.nu), self.k])
+
+    def rhs(self, ubc):
+        """b = [D_I(-F u_b) + D_B u_b; -B u_b] (no body force; u_b zero off the Dirichlet nodes)."""
+        g = self.g
+        ub = self.DB @ np.asarray(ubc, dtype=np.float64)
+        Fub = np.concatenate([self.Fs @ ub[: g.nv], self.Fs @ ub[g.nv:]])
+        return np.concatenate([self.DI @ (-Fub) + ub, -(self.B @ ub)])
+
+    def solve(self, b):
+        """Exact solution with k^T p = 0 (bordered with [0; k])."""
+        x, _ = direct.bordered_solve(self.K, self.kx, b)
+        return x
+
+
+def inflow_data(g: MaskedGrid, profile):
+    """Dirichlet data: u = (profile(y), 0) at the leftmost active column of Dirichlet
+    nodes, zero elsewhere."""
+    ub = np.zeros(g.nu)
+    left = g.dirichlet & np.isclose(g.X2, g.x0)
+    ub[: g.nv][left] = profile(g.Y2[left])
+    return ub
+
+
+def step_inflow(g):
+    return inflow_data(g, lambda y: 4.0 * y * (1.0 - y))
+
+
+def picard(g: MaskedGrid, nu, ubc, steps):
+    """Picard iterates x_1..x_steps (x_1 Stokes) and the nonlinear residuals
+    ||b(u) - K(u) x|| / ||b(u)|| at each iterate."""
+    xs, res = [], []
+    wind = np.zeros(g.nu)
+    for _ in range(steps):
+        s = StepSystem(g, nu, wind)
+        x = s.solve(s.rhs(ubc))
+        xs.append(x)
+        s1 = StepSystem(g, nu, x[: g.nu].copy())
+        b1 = s1.rhs(ubc)
+        res.append(np.linalg.norm(b1 - s1.K @ x) / np.linalg.norm(b1))
+        wind = x[: g.nu].copy()
+    return xs, res
+
+
+def vertical_flux(g: MaskedGrid, u, i):
+    """Flux int u_x dy through the lattice column of Q2 index i (even: element edges),
+    Simpson's rule on each active edge (exact for the Q2 trace)."""
+    ux = u[: g.nv].reshape(g.Ny, g.Nx)
+    h = g.hy
+    tot = 0.0
+    for ey in range(g.ny):
+        ex_l, ex_r = i // 2 - 1, i // 2
+        on = any(0 <= ex < g.nx and g.active[ey, ex] for ex in (ex_l, ex_r))
+        if on:
+            j = 2 * ey
+            tot += h / 6.0 * (ux[j, i] + 4.0 * ux[j + 1, i] + ux[j + 2, i])
+    return tot
+
+
+def dense_gamma2(g: MaskedGrid):
+    """Smallest eigenvalue of B A^{-1} B^T v = lambda M_Q v over the active pressure
+    unknowns orthogonal to k (no hydrostatic mode with an outflow boundary)."""
+    import scipy.linalg as sla
+    s = StepSystem(g, 1.0)
+    act = np.concatenate([g.q1_active, g.p0_active])
+    A = s.Anu.toarray()
+    BI = s.BI.toarray()[act]
+    S = BI @ np.linalg.solve(A, BI.T)
+    M = s.MQ.toarray()[np.ix_(act, act)]
+    W = sla.null_space(s.k[act][None, :])
+    sig = sla.eigh(W.T @ S @ W, W.T @ M @ W, eigvals_only=True)
+    return float(sig[0]), sig

@@ -1,0 +1,87 @@
+"""Pins of the masked-grid inflow-outflow oracle (Sec. 3, Test problem 3).
+
+* With every element active and no outflow, the masked assembly reproduces the
+  square-grid system (itself pinned in test_oracle_fem.py) entry by entry.
+* Poiseuille flow in a channel with a natural outflow is reproduced exactly:
+  u = (1 - y^2, 0) lies in Q2 and p = 2 nu (L - x) in Q1, and the do-nothing
+  condition holds for it (du_x/dx = 0 and p = 0 at x = L).
+* On the step, P0 pressure makes every element conserve mass, so the flux through
+  every vertical grid line equals the inflow flux int_0^1 4y(1-y) dy = 2/3.
+* The null space is one-dimensional: [0; k] (no hydrostatic mode with an outflow).
+* The paper's statements about this problem: the centroid pressures are an order of
+  magnitude smaller than the vertex pressures, and the inf-sup constant of the
+  step domain with its long channel is much smaller than that of the square.
+"""
+import numpy as np
+import pytest
+
+from oracle import fem, infsup, problem, step
+
+
+def test_full_mask_reproduces_square_system():
+    n = 6
+    g = step.MaskedGrid(n, n, 2.0 / n, -1.0, -1.0, np.ones((n, n), dtype=bool), x_out=None)
+    gs = fem.Grid(n)
+    rng = np.random.default_rng(0)
+    wind = rng.standard_normal(gs.nu)
+    a = step.StepSystem(g, 0.03, wind)
+    b = problem.System(gs, 0.03, wind)
+    assert np.array_equal(g.fixed, gs.bnd)
+    assert abs(a.K - b.K).max() <= 1e-14 * abs(b.K).max()
+    assert abs(a.MQ - b.MQ).max() <= 1e-15
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_poiseuille_exact(m):
+    L, nu = 2.0, 0.02
+    g = step.channel_grid(m, L)
+    s = step.StepSystem(g, nu)
+    ub = step.inflow_data(g, lambda y: 1.0 - y ** 2)
+    x = s.solve(s.rhs(ub))
+    u, p1, p0 = x[: g.nu], x[g.nu: g.nu + g.n1], x[g.nu + g.n1:]
+    assert np.abs(u - np.concatenate([1.0 - g.Y2 ** 2, np.zeros(g.nv)])).max() <= 1e-12
+    XI = g.x0 + g.hx * (np.arange(g.n1) % (g.nx + 1))
+    for t, e in enumerate(g.elems):        # pressure function p1 + p0 at the element's vertices
+        nodes = g.q1_conn[t]
+        assert np.abs(p1[nodes] + p0[e] - 2.0 * nu * (L - XI[nodes])).max() <= 1e-12
+
+
+@pytest.mark.parametrize("m", [2, 4])
+def test_step_flux_and_elementwise_conservation(m):
+    g = step.step_grid(m)
+    ub = step.step_inflow(g)
+    xs, res = step.picard(g, 1.0 / 50.0, ub, 5)
+    s = step.StepSystem(g, 1.0 / 50.0)
+    for x in (xs[0], xs[-1]):
+        u = x[: g.nu]
+        fl = np.array([step.vertical_flux(g, u, i) for i in range(0, g.Nx, 2)])
+        assert np.abs(fl - 2.0 / 3.0).max() <= 1e-12, fl
+        div0 = (s.B @ u)[g.n1:][g.p0_active]              # -int_T div u_h
+        assert np.abs(div0).max() <= 1e-13
+    assert all(r1 < 0.6 * r0 for r0, r1 in zip(res, res[1:])), res
+
+
+def test_null_space_is_k_only():
+    g = step.step_grid(1)
+    s = step.StepSystem(g, 1.0 / 50.0, np.random.default_rng(1).standard_normal(g.nu))
+    sv = np.linalg.svd(s.K.toarray(), compute_uv=False)
+    assert sv[-1] <= 1e-12 * sv[0] and sv[-2] >= 1e-6 * sv[0]
+    assert np.abs(s.K @ s.kx).max() <= 1e-13
+
+
+def test_centroid_pressures_an_order_smaller():
+    g = step.step_grid(4)
+    xs, _ = step.picard(g, 1.0 / 50.0, step.step_inflow(g), 5)
+    x = xs[-1]
+    p1 = x[g.nu: g.nu + g.n1][g.q1_active]
+    p0 = x[g.nu + g.n1:][g.p0_active]
+    c = p0.mean()                      # frame split with zero-mean centroid part
+    assert np.abs(p0 - c).max() <= 0.1 * np.abs(p1 + c).max()
+
+
+def test_step_infsup_much_smaller_than_square():
+    g1, _ = step.dense_gamma2(step.step_grid(1))
+    g2, _ = step.dense_gamma2(step.step_grid(2))
+    sq, _ = infsup.dense_gamma2(fem.Grid(8))
+    assert abs(g1 - g2) <= 0.01 * g2
+    assert g2 <= 0.2 * sq and g2 > 0.0
