@@ -21,10 +21,10 @@
 //
 // which is singular by construction (its last pivot vanishes).  The corner
 // entry is gamma_{j+1}^2 / d_j with d_j the last pivot of the LDL^T factorisation
-// of T_j.  Each thread handles one j: it counts the eigenvalues of That below a
-// shift with the Sturm sequence of its pivots (Sylvester's law of inertia) and
-// bisects for the largest eigenvalue below -1e-10 ||That|| (which leaves out the
-// zero eigenvalue whatever rounding does to it).
+// of T_j.  The eigenvalues of That below a shift are counted with the Sturm
+// sequence of its pivots (Sylvester's law of inertia); the estimate is the largest
+// eigenvalue below -1e-10 ||That|| (which leaves out the zero eigenvalue whatever
+// rounding does to it), found by multisection.
 #include <cmath>
 #include "grid.cuh"
 #include "scalars.cuh"
@@ -48,43 +48,80 @@ __device__ int that_count(const double* __restrict__ dl, const double* __restric
   return c;
 }
 
-__global__ void k_est_infsup(const double* __restrict__ dl, const double* __restrict__ gm, int k,
-                             double* __restrict__ est) {
+// One warp per j.  The warp first finds the corner entry, the Gershgorin interval and
+// the number `neg` of eigenvalues below the threshold (lane-parallel where the
+// work is), then multisects: each round the 32 lanes count at 32 equally spaced
+// interior points of [lo, hi), and the interval shrinks to the gap between the
+// first point whose count reaches `neg` and the point before it (33x per round;
+// count(lo) < neg <= count(hi) holds throughout, monotone counts or not).
+__global__ void __launch_bounds__(128) k_est_infsup(const double* __restrict__ dl, const double* __restrict__ gm, int k,
+                                                    double* __restrict__ est) {
   ETH_GRID_DEP_WAIT();
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= k) return;
-  const int m = t + 1;   // Lanczos steps in T_m
-  // last LDL^T pivot of T_m (IEEE arithmetic carries a zero pivot through as inf)
+  const int lane = threadIdx.x & 31;
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (t >= k) return;   // whole warps leave together
+  const int m = t + 1;  // Lanczos steps in T_m
+  // last LDL^T pivot of T_m (every lane; IEEE arithmetic carries a zero pivot through as inf)
   double d = dl[0];
   for (int i = 1; i < m; ++i) d = dl[i] - gm[i - 1] * gm[i - 1] / d;
   const double gl = gm[m - 1];
   const double corner = gl * gl / d;
-  if (!isfinite(corner) || !isfinite(d)) { est[t] = nan(""); return; }
-  // Gershgorin bounds and the norm of That
+  if (!isfinite(corner) || !isfinite(d)) {
+    if (lane == 0) est[t] = nan("");
+    return;
+  }
+  // Gershgorin bounds and the norm of That, rows split over the lanes
   double lo = INFINITY, nrm = 0.0, b2max = 0.0;
-  for (int i = 0; i <= m; ++i) {
+  for (int i = lane; i <= m; i += 32) {
     const double a = i < m ? dl[i] : corner;
     const double r = (i > 0 ? fabs(gm[i - 1]) : 0.0) + (i < m ? fabs(gm[i]) : 0.0);
     lo = fmin(lo, a - r);
     nrm = fmax(nrm, fabs(a) + r);
     if (i < m) b2max = fmax(b2max, gm[i] * gm[i]);
   }
-  if (!(nrm > 0.0) || !isfinite(nrm)) { est[t] = nan(""); return; }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    nrm = fmax(nrm, __shfl_xor_sync(0xffffffffu, nrm, o));
+    b2max = fmax(b2max, __shfl_xor_sync(0xffffffffu, b2max, o));
+  }
+  if (!(nrm > 0.0) || !isfinite(nrm)) {
+    if (lane == 0) est[t] = nan("");
+    return;
+  }
   // smallest pivot magnitude kept (safe minimum times the largest squared coupling)
   const double pivmin = 2.3e-308 * fmax(1.0, b2max);
   double hi = -1e-10 * nrm;
-  const int neg = that_count(dl, gm, m, corner, hi, pivmin);
-  if (neg == 0) { est[t] = nan(""); return; }
-  lo -= 1e-12 * nrm;
-  // the neg-th smallest eigenvalue lies in [lo, hi)
-  for (int it = 0; it < 200; ++it) {
-    const double mid = 0.5 * (lo + hi);
-    if (!(mid > lo && mid < hi)) break;
-    if (that_count(dl, gm, m, corner, mid, pivmin) >= neg) hi = mid; else lo = mid;
-    if (hi - lo <= 2e-16 * fabs(hi)) break;
+  const int neg = that_count(dl, gm, m, corner, hi, pivmin);   // same value in every lane
+  if (neg == 0) {
+    if (lane == 0) est[t] = nan("");
+    return;
   }
-  const double th = 0.5 * (lo + hi);
-  est[t] = th * th - th;
+  lo -= 1e-12 * nrm;
+  for (int round = 0; round < 40; ++round) {
+    const double w = (hi - lo) / 33.0;
+    const double x = lo + (double)(lane + 1) * w;
+    const bool inside = x > lo && x < hi;
+    const bool reach = inside && that_count(dl, gm, m, corner, x, pivmin) >= neg;
+    const unsigned ge = __ballot_sync(0xffffffffu, reach);
+    const unsigned in = __ballot_sync(0xffffffffu, inside);
+    // ge and in are the same in every lane, so every branch below is taken warp-wide
+    double nlo = lo, nhi = hi;
+    unsigned before = in;                 // inside points whose count is below neg
+    if (ge != 0u) {
+      const int first = __ffs(ge) - 1;
+      nhi = __shfl_sync(0xffffffffu, x, first);
+      before = in & ((1u << first) - 1u);
+    }
+    if (before != 0u) nlo = __shfl_sync(0xffffffffu, x, 31 - __clz(before));
+    const bool stuck = (nlo == lo && nhi == hi);
+    lo = nlo;
+    hi = nhi;
+    if (stuck || hi - lo <= 2e-16 * fabs(hi)) break;
+  }
+  if (lane == 0) {
+    const double th = 0.5 * (lo + hi);
+    est[t] = th * th - th;
+  }
 }
 
 }  // namespace eth
@@ -118,8 +155,8 @@ eth_status eth_est_infsup(eth_grid* g, const double* delta_dev, const double* ga
     return ETH_EINVAL;
   }
   if (k == 0) return ETH_OK;
-  const int tb = 64;
-  k_est_infsup<<<(k + tb - 1) / tb, tb, 0, g->s>>>(delta_dev, gamma_dev, k, est_dev);
+  const int warps = 4;   // one warp per estimate, four per CTA
+  k_est_infsup<<<(k + warps - 1) / warps, 32 * warps, 0, g->s>>>(delta_dev, gamma_dev, k, est_dev);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
   return ETH_OK;
