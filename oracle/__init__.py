@@ -30,6 +30,8 @@ two-level pressure approximation"):
                   the two-field pressure and the block-triangular M_3 (Sec. 3.2).
 * ``step``     -- inflow-outflow flow on a masked uniform grid (the flow over a step,
                   Sec. 3 Test problem 3): natural outflow, null space [0; k] only.
+* ``mqcheb``   -- Chebyshev semi-iteration on multicolour symmetric Gauss-Seidel for the
+                  singular M_Q (the M_cheb block of the cheaper preconditioner P_2).
 * ``infsup``   -- the discrete inf-sup constant gamma^2 (dense pencil, Sec. 2.4) and
                   its EST-MINRES estimate from the Lanczos scalars of MINRES.
 
