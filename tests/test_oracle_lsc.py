@@ -100,3 +100,39 @@ def test_lsc_gmres_mesh_robust_and_better_than_m1():
         its_m1.append(info1["its"])
     assert max(its) <= 40 and its[-1] <= 1.5 * its[0], its
     assert all(a < b for a, b in zip(its, its_m1)), (its, its_m1)
+
+
+@pytest.mark.parametrize("n", [4, 8])
+def test_frame_operator_blocks_are_laplacians(n):
+    """The LSC solves with S = B M^{-1} B^T on the frame: its exact block-diagonal part is
+    a mesh-independent preconditioner, and the blocks are spectrally equivalent to the
+    Q1 Laplacian (Q1 block) and to the cell-centred 5-point Laplacian (P0 block), so each
+    can be replaced by a Laplacian V-cycle (the basis of a multigrid LSC solve)."""
+    import scipy.linalg as sla
+    g = fem.Grid(n)
+    s = problem.System(g, 1.0)
+    md = s.Mv.diagonal()
+    m = np.concatenate([md, md])
+    B = s.BI.toarray()
+    S = B @ np.diag(1.0 / m) @ B.T
+    n1 = g.n1
+    W = sla.null_space(np.column_stack([s.e1[g.nu:], s.e0[g.nu:]]).T)
+    Pb = np.zeros_like(S)
+    Pb[:n1, :n1] = S[:n1, :n1]
+    Pb[n1:, n1:] = S[n1:, n1:]
+    lam = sla.eigh(W.T @ S @ W, W.T @ Pb @ W, eigvals_only=True)
+    assert lam.max() / lam.min() <= 5.0
+    K1 = fem.q1_stiffness(g).toarray()
+    W1 = sla.null_space(np.ones((1, n1)))
+    l1 = sla.eigh(W1.T @ S[:n1, :n1] @ W1, W1.T @ K1 @ W1, eigvals_only=True)
+    assert 0.4 <= l1.min() and l1.max() <= 1.6
+    L5 = np.zeros((g.n0, g.n0))
+    for e in range(g.n0):
+        ex, ey = e % n, e // n
+        for dx, dy in ((1, 0), (-1, 0), (0, 1), (0, -1)):
+            if 0 <= ex + dx < n and 0 <= ey + dy < n:
+                L5[e, e] += 1.0
+                L5[e, (ey + dy) * n + ex + dx] -= 1.0
+    W0 = sla.null_space(np.ones((1, g.n0)))
+    l0 = sla.eigh(W0.T @ S[n1:, n1:] @ W0, W0.T @ L5 @ W0, eigvals_only=True)
+    assert 3.0 <= l0.min() and l0.max() <= 5.0
