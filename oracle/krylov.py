@@ -274,13 +274,15 @@ class PCD1:
         return np.concatenate([zu, zp])
 
 
-def two_stage(sys, b, eta=1e-6, c=10.0, restart=50, maxit=2000, x0=None):
+def two_stage(sys, b, eta=1e-6, c=10.0, restart=50, maxit=2000, x0=None, pcd_cls=None, m1_cls=None):
     """Two-stage PCD solve of Sec. 3.1.
 
     Step I: GMRES + PCD1 on the reduced system [F B1^T; B1 0][u; q1] = [f; g1]
     until its residual is <= c*eta*||b_red||.  Step II: GMRES + M1 on the full
     system from [u1*, q1*, 0] until ||b - K x|| <= eta*||b||.
-    ``x0`` defaults to the lifted boundary data (interior zero).
+    ``x0`` defaults to the lifted boundary data (interior zero).  ``pcd_cls`` and
+    ``m1_cls`` replace the Step I and Step II preconditioner classes (default PCD1
+    and M1, for the enclosed square; other domains bring their own).
     Returns (x, info) with the iteration counts and the Prop. 2 quantities
     (||z*||^2 and the bound c^2 eta^2 ||b_red||^2 + ||r0*||^2, where r0* is the
     P0 block of the residual at the switch; it equals B0 u1* when g0 = 0).
@@ -291,7 +293,7 @@ def two_stage(sys, b, eta=1e-6, c=10.0, restart=50, maxit=2000, x0=None):
         x0 = np.concatenate([sys.DB @ b[:nu_], np.zeros(g.np_)])
     bred = b[: nu_ + n1]
     Kred = lambda v: sys.K1 @ v
-    pcd = PCD1(sys)
+    pcd = (pcd_cls or PCD1)(sys)
     nb_red = np.linalg.norm(bred)
     x1, info1 = gmres(Kred, pcd, bred, x0[: nu_ + n1], c * eta * nb_red, restart, maxit)
     xs = np.concatenate([x1, np.zeros(g.n0)])
@@ -299,7 +301,7 @@ def two_stage(sys, b, eta=1e-6, c=10.0, restart=50, maxit=2000, x0=None):
     z2 = float(np.dot(zs, zs))
     r0 = zs[nu_ + n1:]
     bound = (c * eta * nb_red) ** 2 + float(np.dot(r0, r0))
-    m1 = M1(sys)
+    m1 = (m1_cls or M1)(sys)
     x, info2 = gmres(lambda v: sys.K @ v, m1, b, xs, eta * np.linalg.norm(b), restart, maxit)
     return x, {"its1": info1["its"], "its2": info2["its"], "res1": info1["res"],
                "res2": info2["res"], "z_star_sq": z2, "prop2_bound": bound,

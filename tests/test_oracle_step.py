@@ -85,3 +85,60 @@ def test_step_infsup_much_smaller_than_square():
     sq, _ = infsup.dense_gamma2(fem.Grid(8))
     assert abs(g1 - g2) <= 0.01 * g2
     assert g2 <= 0.2 * sq and g2 > 0.0
+
+
+def test_inflow_robin_closed_form():
+    """For a constant wind (c, 0) entering a channel at x = 0, the inflow boundary matrix
+    is the 1D Q1 mass of the inflow edge times c: total c * (edge length) = 2c, symmetric,
+    nothing on the edges the wind leaves through or runs along, and nothing for zero wind."""
+    g = step.channel_grid(3, 2.0)
+    c = 0.7
+    wind = np.concatenate([np.full(g.nv, c), np.zeros(g.nv)])
+    R = step.inflow_robin_q1(g, wind).toarray()
+    assert abs(R.sum() - 2.0 * c) <= 1e-13 and np.allclose(R, R.T, atol=1e-15)
+    I = np.arange(g.n1) % (g.nx + 1)
+    assert np.abs(R[I != 0]).max() == 0.0 and np.abs(R[:, I != 0]).max() == 0.0
+    h = g.hy
+    col = R[np.ix_(I == 0, I == 0)]
+    assert np.isclose(col[0, 0], c * h / 3.0) and np.isclose(col[1, 1], 2.0 * c * h / 3.0)
+    assert np.isclose(col[0, 1], c * h / 6.0)
+    # reversed, the wind enters through the right edge instead
+    Rr = step.inflow_robin_q1(g, -wind).toarray()
+    assert np.abs(Rr[I != g.nx]).max() == 0.0 and abs(Rr.sum() - 2.0 * c) <= 1e-13
+    assert np.abs(step.inflow_robin_q1(g, 0.0 * wind).toarray()).max() == 0.0
+
+
+def test_pcd_needs_the_inflow_term():
+    """With natural conditions only (no inflow term: the Stokes system) the PCD Schur
+    approximation annihilates the Q1 mass image of the constants; with the Oseen wind
+    and its inflow term it does not (the reason for the reading)."""
+    g = step.step_grid(2)
+    one = g.q1_active.astype(float)
+    s0 = step.StepSystem(g, 1.0 / 50.0)
+    z0 = step.StepPCD1(s0).schur_inv(s0.Qk @ one)
+    assert np.abs(z0).max() <= 1e-10
+    xs, _ = step.picard(g, 1.0 / 50.0, step.step_inflow(g), 2)
+    s1 = step.StepSystem(g, 1.0 / 50.0, xs[-1][: g.nu].copy())
+    z1 = step.StepPCD1(s1).schur_inv(s1.Qk @ one)
+    assert np.abs(z1).max() >= 1e-3
+
+
+def test_step_two_stage_pcd():
+    """The two-stage method (Sec. 3.1) on the Oseen step problem after five Picard steps:
+    converges to the direct solution, Prop. 2 holds at the switch, and Step I needs a
+    mesh-independent number of iterations (the paper's PCD histories are mesh independent)."""
+    its1 = []
+    for m in (2, 4):
+        g = step.step_grid(m)
+        ub = step.step_inflow(g)
+        xs, _ = step.picard(g, 1.0 / 50.0, ub, 5)
+        s = step.StepSystem(g, 1.0 / 50.0, xs[-1][: g.nu].copy())
+        b = s.rhs(ub)
+        x, info = step.two_stage(s, b, eta=1e-6, c=10.0)
+        assert np.linalg.norm(b - s.K @ x) <= 1e-6 * np.linalg.norm(b) * 1.0001
+        xd = s.solve(b)
+        xc = x - (s.kx @ x) / (s.kx @ s.kx) * s.kx
+        assert np.linalg.norm(xc - xd) <= 1e-4 * np.linalg.norm(xd)
+        assert info["z_star_sq"] <= info["prop2_bound"] * (1.0 + 1e-10)
+        its1.append(info["its1"])
+    assert max(its1) <= 25 and abs(its1[1] - its1[0]) <= 5, its1
