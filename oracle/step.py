@@ -317,3 +317,42 @@ def two_stage(sys, b, eta=1e-6, c=10.0, restart=50, maxit=2000):
     system with StepPCD1, Step II on the full system with StepM1)."""
     return krylov.two_stage(sys, b, eta, c, restart, maxit, pcd_cls=StepPCD1, m1_cls=StepM1)
 
+
+class StepLSC:
+    """The LSC preconditioner M_3 (Sec. 3.2, Eq. lsc-definition and nse-precon-lsc) on
+    the masked grid, with H = M (plain LSC): both frame products B M^{-1} B^T are
+    singular along k alone (outflow), inactive pressure unknowns keep identity rows."""
+
+    def __init__(self, sys):
+        from . import lsc
+        self.sys = sys
+        g = sys.g
+        md = sys.Mv.diagonal()
+        m = np.concatenate([md, md])
+        self.minv = np.where(m > 0.0, 1.0 / np.where(m > 0.0, m, 1.0), 0.0)
+        self.B = sys.BI
+        pin = sp.diags(np.concatenate([~g.q1_active, ~g.p0_active]).astype(float))
+        S = (self.B @ sp.diags(self.minv) @ self.B.T + pin).tocsr()
+        self.BMB = lsc._ConstrainedSolve(S, sys.k[:, None])
+        self.Fsolve = krylov._LU(sys.F)
+
+    def schur_inv(self, rp):
+        y = self.BMB(rp)
+        t = self.B @ (self.minv * (self.sys.F @ (self.minv * (self.B.T @ y))))
+        return self.BMB(t)
+
+    def __call__(self, r):
+        s = self.sys
+        nu_ = s.g.nu
+        zp = -self.schur_inv(r[nu_:])
+        zu = self.Fsolve(r[:nu_] - s.BI.T @ zp)
+        return np.concatenate([zu, zp])
+
+
+def lsc_solve(sys, b, tol=1e-6, restart=50, maxit=2000):
+    """GMRES with the right preconditioner M_3 (LSC) on the full masked-grid system from
+    the lifted boundary data; stops at ||b - K x|| <= tol ||b||."""
+    g = sys.g
+    x0 = np.concatenate([sys.DB @ b[: g.nu], np.zeros(g.np_)])
+    return krylov.gmres(lambda v: sys.K @ v, StepLSC(sys), b, x0, tol * np.linalg.norm(b), restart, maxit)
+

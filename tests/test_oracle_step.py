@@ -142,3 +142,23 @@ def test_step_two_stage_pcd():
         assert info["z_star_sq"] <= info["prop2_bound"] * (1.0 + 1e-10)
         its1.append(info["its1"])
     assert max(its1) <= 25 and abs(its1[1] - its1[0]) <= 5, its1
+
+
+def test_step_lsc_mesh_robust():
+    """GMRES with the LSC preconditioner M_3 on the Oseen step problem reaches the direct
+    solution in a mesh-independent number of steps (the paper: LSC gives good results
+    for Q2-Q1*)."""
+    its = []
+    for m in (2, 4, 8):
+        g = step.step_grid(m)
+        ub = step.step_inflow(g)
+        xs, _ = step.picard(g, 1.0 / 50.0, ub, 5)
+        s = step.StepSystem(g, 1.0 / 50.0, xs[-1][: g.nu].copy())
+        b = s.rhs(ub)
+        x, info = step.lsc_solve(s, b, tol=1e-6)
+        assert np.linalg.norm(b - s.K @ x) <= 1e-6 * np.linalg.norm(b) * 1.0001
+        xd = s.solve(b)
+        xc = x - (s.kx @ x) / (s.kx @ s.kx) * s.kx
+        assert np.linalg.norm(xc - xd) <= 1e-4 * np.linalg.norm(xd)
+        its.append(info["its"])
+    assert max(its) <= 20 and max(its) - min(its) <= 4, its
