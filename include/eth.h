@@ -260,8 +260,8 @@ eth_status eth_lanczos(eth_grid* g, int cap, double* delta_dev, double* gamma_de
  * singular).  With the exact block preconditioner P_1 (opts a_exact = 1, mq_mode
  * = ETH_MQ_EXACT) the estimates approach gamma^2 from above; with approximate
  * blocks they estimate the corresponding quantity of that preconditioner.
- * Asynchronous on g's stream; g only supplies the stream.  One device thread
- * per j, each O(j) work per bisection step. */
+ * Asynchronous on g's stream; g only supplies the stream.  One warp per j:
+ * each multisection round evaluates 32 Sturm counts of O(j) work. */
 eth_status eth_est_infsup(eth_grid* g, const double* delta_dev, const double* gamma_dev, int k, double* est_dev);
 
 /* Batched solves of independent instances (each created with its own handle,
