@@ -162,3 +162,28 @@ def test_step_lsc_mesh_robust():
         assert np.linalg.norm(xc - xd) <= 1e-4 * np.linalg.norm(xd)
         its.append(info["its"])
     assert max(its) <= 20 and max(its) - min(its) <= 4, its
+
+
+@pytest.mark.parametrize("m", [1, 2])
+def test_step_est_minres_reaches_dense_gamma2(m):
+    """EST-MINRES (Sec. 2.4) on the Stokes step problem with the exact blocks
+    blkdiag(A, M_Q) (M_Q augmented with k, identity rows for inactive unknowns) reaches
+    the dense inf-sup constant of the step from above: a second route to the value
+    compared with the square's."""
+    import scipy.sparse as sp
+    from oracle import krylov
+    g = step.step_grid(m)
+    s = step.StepSystem(g, 1.0)
+    b = s.rhs(step.step_inflow(g))
+    Alu = krylov._LU(s.Anu)
+    pin = sp.diags(np.concatenate([~g.q1_active, ~g.p0_active]).astype(float))
+    aug = sp.bmat([[s.MQ + pin, sp.csr_matrix(s.k[:, None])], [sp.csr_matrix(s.k[None, :]), None]])
+    Mlu = krylov._LU(aug.tocsc())
+    P = lambda r: np.concatenate([Alu(r[: g.nu]), Mlu(np.concatenate([r[g.nu:], [0.0]]))[:-1]])
+    x0 = np.concatenate([s.DB @ b[: g.nu], np.zeros(g.np_)])
+    _, info = krylov.minres(lambda v: s.K @ v, P, b, x0, tol=1e-12, maxit=2000)
+    h = infsup.est_history(info["delta"], info["gamma"])
+    g2, _ = step.dense_gamma2(g)
+    fin = h[np.isfinite(h)]
+    assert np.all(fin >= g2 * (1 - 1e-8))
+    assert abs(h[-1] - g2) <= 1e-6 * g2
