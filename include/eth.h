@@ -31,6 +31,10 @@
  * streams (graphs need a capturable stream), which wait for the work already on
  * the user stream and are joined back to it, and synchronise once at the end to
  * fill eth_stats.
+ * Devices: a handle belongs to the CUDA device that is current when it is
+ * created (its workspace lives there, and its stream must belong to it); every
+ * call on a handle makes that device current for its duration and restores the
+ * caller's current device on return.
  * Errors: every call returns an eth_status; no exception crosses the ABI.
  * eth_last_error() returns a thread-local message for the last failure.
  */
@@ -184,9 +188,15 @@ eth_status eth_solve_host(eth_grid* g, const eth_opts* opts, const double* f_nod
                           const double* ubc_host, double* u_host, double* p_host,
                           eth_stats* stats);
 
-/* Adjoint solve K^T [l_u; l_p] = [r_u; r_p] (r_p must have zero sums on the
- * Q1 and P0 blocks).  Stokes: same solver (K symmetric).  Oseen: the two-stage
- * solver applied to K^T = [F^T B^T; B 0] with PCD built on F1^T. */
+/* Adjoint solve K^T [l_u; l_p] = [r_u; r_p].  Stokes: same solver (K
+ * symmetric).  Oseen: the two-stage solver applied to K^T = [F^T B^T; B 0]
+ * with PCD built on F1^T.  K^T is singular on the same pressure null space as K
+ * (span{e1, e0}, Sec. 3 Test problem 4), so the solver removes the e1 and e0
+ * components (the sums of the Q1 and P0 blocks) of r_p first, as eth_solve does
+ * for its right-hand side; this is exactly the adjoint of the projection that
+ * makes eth_solve's pressure canonical.  When the removed part exceeds
+ * 1e-8 ||[r_u; r_p]|| the call returns ETH_EINCONSISTENT with the solution of
+ * the projected system; l_p is canonical (zero block sums). */
 eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru_dev,
                              const double* rp_dev, double* lu_dev, double* lp_dev,
                              eth_stats* stats);
@@ -215,14 +225,31 @@ eth_status eth_adjoint_gradients(eth_grid* g, const double* lu_dev, const double
  * [x0,x1] x [y0,y1] and *dot_dev = <K x, x> (FP64), with FP32 element
  * arithmetic when fp32 != 0.  x_dev, y_dev: N_t FP64 device vectors; dot_dev:
  * one FP64 device value; all owned by the caller.  Nothing is allocated: the
- * reduction scratch is a fixed file-scope device array (32768 block partials,
- * so n <= 2048; larger n returns ETH_EINVAL) that every GPU loading the library
+ * reduction scratch is a fixed file-scope device array of 32768 block partials
+ * (one per 32 x 8 element tile, ceil(n/31) * ceil(n/7) tiles, so every even n up
+ * to 2666 fits; larger n returns ETH_EINVAL) that every GPU loading the library
  * holds until exit.  The first call on a device looks the array's address up
  * (cudaGetSymbolAddress) and should come before any stream capture.  All calls
  * share the array: calls whose kernels overlap on the GPU race.  The paper has
  * no counterpart of this entry point. */
 eth_status eth_apply_k_dot_static(int n, double x0, double x1, double y0, double y1, double nu, int fp32,
                                   const double* x_dev, double* y_dev, double* dot_dev, void* cuda_stream);
+
+/* Pressure convection-diffusion Schur approximation of Step I alone (Sec. 3.1,
+ * Eq. discrete-commutator1x): zp = M_S^{-1} rp = Ap^+ F1 Q1^{-1} rp on the Q1
+ * pressure, with Q1 the Q1 mass matrix, F1 = nu K1 + N1(w) the Q1
+ * convection-diffusion matrix (adjoint != 0: its transpose, as the adjoint
+ * Oseen solve uses), Ap = B1 Md^{-1} B1^T over interior velocity columns (Md
+ * the diagonal of the velocity mass matrix) and Ap^+ its inverse on mean-free
+ * vectors.  The Oseen solver applies -M_S^{-1} inside its block-triangular
+ * preconditioner with 10 Chebyshev steps for Q1^{-1} and 2 PCG steps for Ap^+;
+ * here cheb_steps (0..1000) and ap_its (1..1000) choose them, so large counts
+ * give the exact block.  rp_dev, zp_dev: device, N_1 FP64 each (caller-owned);
+ * zp has zero mean.  fp32 != 0 runs the inner steps in FP32.  g must be an
+ * ETH_OSEEN grid with coefficients set; ETH_EINVAL otherwise.  Asynchronous on
+ * g's stream. */
+eth_status eth_apply_pcd(eth_grid* g, int adjoint, int fp32, int cheb_steps, int ap_its, const double* rp_dev,
+                         double* zp_dev);
 
 /* Picard iteration for the steady Navier-Stokes problem (Sec. 3: the Oseen
  * systems are its linearisations).  g must be an ETH_OSEEN grid whose viscosity

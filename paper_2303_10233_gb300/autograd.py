@@ -8,22 +8,17 @@ the same MINRES for symmetric Stokes, the two-stage PCD GMRES on
 
     dL/df_nodal = M_v D_I l_u,      dL/dnu = -(D_I l_u)^T A u
 
-are formed by eth_adjoint_gradients.  Only argument marshalling happens here.
+are formed by eth_adjoint_gradients.  The forward pressure is canonical (its
+constant Q1 and P0 components removed), so the gradient reaching the adjoint
+system is the projected g_p; eth_solve_adjoint performs that projection itself
+and reports a removed component as ETH_EINCONSISTENT, which is expected here.
+Only argument marshalling happens in this module.
 """
 from __future__ import annotations
 
 import torch
 
 from . import eth
-
-
-def _project_pressure(gp, n1):
-    """Remove the constant-Q1 and constant-P0 components (the adjoint system is
-    consistent only for a pressure right-hand side with zero block sums)."""
-    gp = gp.clone()
-    gp[:n1] -= gp[:n1].mean()
-    gp[n1:] -= gp[n1:].mean()
-    return gp
 
 
 class EthSolve(torch.autograd.Function):
@@ -48,9 +43,8 @@ class EthSolve(torch.autograd.Function):
         gu = torch.zeros_like(u) if gu is None else gu.contiguous()
         if gp is None:
             gp = torch.zeros(grid.n1 + grid.n0, dtype=torch.float64, device=u.device)
-        gp = _project_pressure(gp.contiguous(), grid.n1)
-        lu, lp, st = grid.solve_adjoint(gu, gp, **ctx.opts)
-        if st["status"] not in (0,):
+        lu, lp, st = grid.solve_adjoint(gu, gp.contiguous(), **ctx.opts)
+        if st["status"] not in (0, 6):   # 6: the pressure gradient's null-space part was projected out
             raise eth.EthError(st["status"], f"adjoint solve did not converge: {st}")
         gf, gnu = grid.adjoint_gradients(lu, u)
         gnu_t = torch.tensor(gnu, dtype=torch.float64, device=u.device) if ctx.nu_is_tensor else None

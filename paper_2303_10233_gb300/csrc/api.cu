@@ -85,7 +85,10 @@ eth_status eth_grid_create(int n, double x0, double x1, double y0, double y1, et
   if (n < 2 || (n & 1) || n > 8192) { set_error("eth_grid_create: n=%d must be even, 2 <= n <= 8192", n); return ETH_EINVAL; }
   if (!(x1 > x0) || !(y1 > y0)) { set_error("eth_grid_create: empty domain"); return ETH_EINVAL; }
   if (kind != ETH_STOKES && kind != ETH_OSEEN) { set_error("eth_grid_create: bad kind"); return ETH_EINVAL; }
+  int dev = 0;
+  ETH_CUDA(cudaGetDevice(&dev));
   eth_grid* g = new eth_grid();
+  g->dev = dev;
   g->n = n; g->x0 = x0; g->x1 = x1; g->y0 = y0; g->y1 = y1;
   g->hx = (x1 - x0) / n; g->hy = (y1 - y0) / n;
   g->kind = kind;
@@ -120,6 +123,7 @@ eth_status eth_grid_create(int n, double x0, double x1, double y0, double y1, et
 
 void eth_grid_destroy(eth_grid* g) {
   if (!g) return;
+  DeviceGuard guard(g->dev);
   if (g->s) cudaStreamSynchronize(g->s); else cudaDeviceSynchronize();
   solver_free(g);
   cudaFree(g->b); cudaFree(g->ubc); cudaFree(g->tmp); cudaFree(g->tmp2);
@@ -134,6 +138,7 @@ eth_status eth_set_coefficients(eth_grid* g, double nu, const double* wind_dev) 
   if (!(nu > 0.0) || !std::isfinite(nu)) { set_error("eth_set_coefficients: nu=%g must be > 0", nu); return ETH_EINVAL; }
   if (g->kind == ETH_OSEEN && !wind_dev) { set_error("eth_set_coefficients: Oseen needs a wind"); return ETH_EINVAL; }
   if (g->kind == ETH_STOKES && wind_dev) { set_error("eth_set_coefficients: Stokes takes no wind"); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   g->nu = nu;
   if (wind_dev) {
     const size_t nu2 = 2 * (size_t)g->nv;
@@ -149,6 +154,7 @@ eth_status eth_set_coefficients(eth_grid* g, double nu, const double* wind_dev) 
 eth_status eth_set_rhs(eth_grid* g, const double* f, const double* ubc) {
   if (!g || !f || !ubc) { set_error("eth_set_rhs: NULL argument"); return ETH_EINVAL; }
   if (!g->has_coef) { set_error("eth_set_rhs: call eth_set_coefficients first"); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   ETH_TRY(assemble_rhs(g, f, ubc));
   g->has_rhs = true;
   return ETH_OK;
@@ -157,6 +163,7 @@ eth_status eth_set_rhs(eth_grid* g, const double* f, const double* ubc) {
 eth_status eth_get_rhs(eth_grid* g, double* b_dev) {
   if (!g || !b_dev) { set_error("eth_get_rhs: NULL argument"); return ETH_EINVAL; }
   if (!g->has_rhs) { set_error("eth_get_rhs: no right-hand side set"); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   ETH_CUDA(cudaMemcpyAsync(b_dev, g->b, (size_t)g->nt * 8, cudaMemcpyDeviceToDevice, g->s));
   return ETH_OK;
 }
@@ -168,6 +175,7 @@ eth_status eth_apply(eth_grid* g, eth_op op, int fp32, const double* x, double* 
     return ETH_EINVAL;
   }
   if ((int)op < 0 || (int)op > (int)ETH_OP_K1T) { set_error("eth_apply: bad operator %d", (int)op); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   return op_apply(g, op, fp32 != 0, x, y);
 }
 

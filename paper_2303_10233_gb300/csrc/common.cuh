@@ -7,6 +7,7 @@
 // linear Lagrange at {0, 1} for the Q1 pressure, indicator for P0.
 #pragma once
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <cstdlib>
@@ -233,5 +234,47 @@ eth_status cuda_status(cudaError_t e, const char* what);
   } while (0)
 
 inline unsigned cdiv(long a, long b) { return (unsigned)((a + b - 1) / b); }
+
+// Dynamic shared memory above 48 KB is enabled per kernel AND per device
+// (cudaFuncSetAttribute acts on the current device).  One SmemAttr per kernel
+// records, per device, the largest size enabled so far; the first launch of
+// that kernel on each device (and any larger request) sets the attribute.
+constexpr int ETH_MAX_DEVICES = 64;
+struct SmemAttr {
+  std::atomic<int> bytes[ETH_MAX_DEVICES];
+};
+template <class K>
+inline cudaError_t smem_attr(K kern, size_t bytes, SmemAttr& a) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool tracked = dev >= 0 && dev < ETH_MAX_DEVICES;
+  if (tracked && (int)bytes <= a.bytes[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess || !tracked) return e;
+  int prev = a.bytes[dev].load(std::memory_order_relaxed);
+  while (prev < (int)bytes && !a.bytes[dev].compare_exchange_weak(prev, (int)bytes)) {
+  }
+  return cudaSuccess;
+}
+
+// Makes a handle's device current for the duration of an entry point and
+// restores the caller's device afterwards (all device memory and streams of a
+// handle belong to the device that was current at its creation).
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+    else if (err == cudaSuccess) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+#define ETH_ON_DEVICE(g)                                                          \
+  ::eth::DeviceGuard eth_dev_guard_((g)->dev);                                    \
+  if (eth_dev_guard_.err != cudaSuccess) return ::eth::cuda_status(eth_dev_guard_.err, "cudaSetDevice")
 
 }  // namespace eth

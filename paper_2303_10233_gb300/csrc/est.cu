@@ -136,6 +136,7 @@ eth_status eth_lanczos(eth_grid* g, int cap, double* delta_dev, double* gamma_de
     return ETH_EINVAL;
   }
   if (g->kind != ETH_STOKES) { set_error("eth_lanczos: Lanczos coefficients are kept by Stokes (MINRES) solves"); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   ETH_CUDA(cudaMemcpyAsync(&g->sch->lz_n, &g->sc->lz_n, sizeof(int), cudaMemcpyDeviceToHost, g->s));
   ETH_CUDA(cudaMemcpyAsync(&g->sch->lz_runs, &g->sc->lz_runs, sizeof(int), cudaMemcpyDeviceToHost, g->s));
   ETH_CUDA(cudaStreamSynchronize(g->s));
@@ -155,6 +156,7 @@ eth_status eth_est_infsup(eth_grid* g, const double* delta_dev, const double* ga
     return ETH_EINVAL;
   }
   if (k == 0) return ETH_OK;
+  ETH_ON_DEVICE(g);
   const int warps = 4;   // one warp per estimate, four per CTA
   k_est_infsup<<<(k + warps - 1) / warps, 32 * warps, 0, g->s>>>(delta_dev, gamma_dev, k, est_dev);
   ETH_CUDA(cudaGetLastError());

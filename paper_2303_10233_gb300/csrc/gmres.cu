@@ -701,15 +701,18 @@ static eth_status vel_part(eth_grid* g, Work* w, const eth_opts* o, const double
   return vcycle_vel<T>(g, adj ? vel_hier_t<T>(w) : vel_hier<T>(w), G->t, zu, o->mg_pre, o->mg_post, done, nullptr, 0);
 }
 
-// Step I preconditioner on [r_u; r_p1]: z_p = -Ap^+ F1 Q1^{-1} r_p, z_u = V_F(r_u - B1^T z_p)
+// Q1 PCD Schur approximation (Sec. 3.1, Eq. discrete-commutator1x):
+// zp = scale * M_S^{-1} rp = scale * Ap^+ F1 Q1^{-1} rp (mean-free), Q1^{-1} by
+// `cheb` Chebyshev steps, Ap^+ by `its` PCG steps; F1 (or F1^T, adjoint set-up)
+// with the element convection matrices of pcd_setup.
 template <class T>
-static eth_status precond_pcd(eth_grid* g, Work* w, const eth_opts* o, const double* r, double* z, const int* done, bool adj) {
+static eth_status pcd_schur(eth_grid* g, Work* w, const double* rp, double* zp, double scale, int cheb, int its,
+                            const int* done) {
   GMRESWork* G = w->gm;
-  const size_t nu2 = 2 * (size_t)g->nv;
   const int m = g->n1;
   T* a = pv<T>(G, 1);
   T* fa = pv<T>(G, 5);
-  ETH_TRY(q1_mass_inv<T>(g, G, r + nu2, a, 10, done));
+  ETH_TRY(q1_mass_inv<T>(g, G, rp, a, cheb, done));
   {
     Q1Params<T, T, T> P{};
     P.n = g->n; P.hx = (T)g->hx; P.hy = (T)g->hy; P.cm = 0; P.ck = (T)g->nu; P.c1 = 0;
@@ -724,11 +727,19 @@ static eth_status precond_pcd(eth_grid* g, Work* w, const eth_opts* o, const dou
   k_copy_t<T><<<gb(m), 256, 0, g->s>>>(m, fa, rhs);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
-  ETH_TRY(ap_solve<T>(g, w, rhs, sol, 2, done));
+  ETH_TRY(ap_solve<T>(g, w, rhs, sol, its, done));
   k_sum_t<T><<<gb(m), 256, 0, g->s>>>(m, sol, G->part, G->ticket + 2, &G->gs->pcg[3]);
-  k_pcd_out<T><<<gb(m), 256, 0, g->s>>>(m, sol, z + nu2, G->gs, -1.0);
+  k_pcd_out<T><<<gb(m), 256, 0, g->s>>>(m, sol, zp, G->gs, scale);
   ETH_CUDA(cudaGetLastError());
   g->launches += 2;
+  return ETH_OK;
+}
+
+// Step I preconditioner on [r_u; r_p1]: z_p = -Ap^+ F1 Q1^{-1} r_p, z_u = V_F(r_u - B1^T z_p)
+template <class T>
+static eth_status precond_pcd(eth_grid* g, Work* w, const eth_opts* o, const double* r, double* z, const int* done, bool adj) {
+  const size_t nu2 = 2 * (size_t)g->nv;
+  ETH_TRY(pcd_schur<T>(g, w, r + nu2, z + nu2, -1.0, 10, 2, done));
   return vel_part<T>(g, w, o, r, z + nu2, false, z, done, adj);
 }
 
@@ -965,6 +976,18 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
   return st->relres_true <= eta * (1.0 + 1e-9) ? ETH_OK : ETH_ENOTCONV;
 }
 
+// M_S^{-1} rp alone, with chosen inner step counts (eth_apply_pcd).
+template <class T>
+static eth_status apply_pcd_t(eth_grid* g, Work* w, bool adjoint, int cheb, int its, const double* rp, double* zp) {
+  eth_opts o;
+  eth_default_opts(&o);
+  o.precision = sizeof(T) == 4 ? ETH_MIXED : ETH_FP64;
+  ETH_TRY(ensure_hier<T>(g, w, &o));
+  if (!w->gm) ETH_TRY(gm_alloc(g, w, 1));
+  ETH_TRY(pcd_setup<T>(g, w, adjoint));
+  return pcd_schur<T>(g, w, rp, zp, 1.0, cheb, its, nullptr);
+}
+
 eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* bsrc) {
   const int m = std::max(1, std::min(std::max(o->restart, o->restart_max), GM_MAX));
   ETH_TRY(gm_alloc(g, w, m));
@@ -988,3 +1011,22 @@ eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, b
 }
 
 }  // namespace eth
+
+using namespace eth;
+
+extern "C" eth_status eth_apply_pcd(eth_grid* g, int adjoint, int fp32, int cheb_steps, int ap_its, const double* rp_dev,
+                                    double* zp_dev) {
+  if (!g || !rp_dev || !zp_dev) { set_error("eth_apply_pcd: NULL argument"); return ETH_EINVAL; }
+  if (g->kind != ETH_OSEEN) { set_error("eth_apply_pcd: the PCD block belongs to ETH_OSEEN grids"); return ETH_EINVAL; }
+  if (!g->has_coef) { set_error("eth_apply_pcd: call eth_set_coefficients first"); return ETH_EINVAL; }
+  if (cheb_steps < 0 || cheb_steps > 1000 || ap_its < 1 || ap_its > 1000) {
+    set_error("eth_apply_pcd: cheb_steps=%d (0..1000) or ap_its=%d (1..1000) out of range", cheb_steps, ap_its);
+    return ETH_EINVAL;
+  }
+  ETH_ON_DEVICE(g);
+  Work* w;
+  ETH_TRY(work_get(g, &w));
+  StreamSwap guard(g, w);
+  return fp32 ? apply_pcd_t<float>(g, w, adjoint != 0, cheb_steps, ap_its, rp_dev, zp_dev)
+              : apply_pcd_t<double>(g, w, adjoint != 0, cheb_steps, ap_its, rp_dev, zp_dev);
+}

@@ -41,6 +41,7 @@ struct Hier {
 
 struct eth_grid {
   int n = 0;
+  int dev = 0;                // CUDA device current at creation (owns every allocation below)
   double x0 = -1, x1 = 1, y0 = -1, y1 = 1, hx = 0, hy = 0;
   eth_kind kind = ETH_STOKES;
   cudaStream_t s = nullptr;

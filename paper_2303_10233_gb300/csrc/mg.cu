@@ -1192,12 +1192,9 @@ static eth_status q2_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, int pre, int
   const size_t ainv_bytes = (size_t)H.ncoarse * H.ncoarse * sizeof(T);
   const int ainv_smem = (ainv_bytes <= 48 * 1024 && smem + ainv_bytes <= 200 * 1024) ? 1 : 0;
   if (ainv_smem) smem += ainv_bytes;
-  static size_t set = 0;   // largest dynamic shared memory requested so far (static shared memory counts too)
+  static SmemAttr attr;   // largest dynamic shared memory enabled so far, per device
   if (smem > 200 * 1024) { set_error("multigrid: coarse levels exceed shared memory"); return ETH_EINVAL; }
-  if (smem > set) {
-    ETH_CUDA(cudaFuncSetAttribute(k_q2_coarse_vc<T, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    set = smem;
-  }
+  ETH_CUDA(smem_attr(k_q2_coarse_vc<T, FL>, smem, attr));
   k_q2_coarse_vc<T, FL><<<1, 512, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, pre, post, done,
                                                   ainv_smem);
   ETH_CUDA(cudaGetLastError());
@@ -1282,12 +1279,9 @@ static eth_status q1_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, const int* d
   const size_t ainv_bytes = (size_t)H.ncoarse * H.ncoarse * sizeof(T);
   const int ainv_smem = (ainv_bytes <= 48 * 1024 && smem + ainv_bytes <= 200 * 1024) ? 1 : 0;
   if (ainv_smem) smem += ainv_bytes;
-  static size_t set = 0;
+  static SmemAttr attr;
   if (smem > 200 * 1024) { set_error("multigrid: Q1 coarse levels exceed shared memory"); return ETH_EINVAL; }
-  if (smem > set) {
-    ETH_CUDA(cudaFuncSetAttribute(k_q1_coarse_vc<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    set = smem;
-  }
+  ETH_CUDA(smem_attr(k_q1_coarse_vc<T>, smem, attr));
   k_q1_coarse_vc<T><<<1, 1024, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, done,
                                               ainv_smem);
   ETH_CUDA(cudaGetLastError());

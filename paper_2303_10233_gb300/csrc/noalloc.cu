@@ -17,7 +17,9 @@
 
 namespace eth {
 
-// at most ETH_NOALLOC_MAX_BLOCKS tile CTAs per call (n <= 2048 needs 19,607)
+// at most ETH_NOALLOC_MAX_BLOCKS tile CTAs per call: ceil(n/31) * ceil(n/7) tiles of
+// 32 x 8 elements, e.g. 67 * 293 = 19,631 at n = 2048; the largest even n that fits is 2666
+// (86 * 381 = 32,766)
 constexpr int ETH_NOALLOC_MAX_BLOCKS = 32768;
 struct NoAllocScratch {
   double partials[ETH_NOALLOC_MAX_BLOCKS];
@@ -77,8 +79,8 @@ extern "C" eth_status eth_apply_k_dot_static(int n, double x0, double x1, double
   if (n < 2 || (n & 1)) { set_error("eth_apply_k_dot_static: n=%d must be even and >= 2", n); return ETH_EINVAL; }
   if (!(x1 > x0) || !(y1 > y0) || !(nu > 0.0)) { set_error("eth_apply_k_dot_static: bad domain or viscosity"); return ETH_EINVAL; }
   if (q2_blocks(n) > ETH_NOALLOC_MAX_BLOCKS) {
-    set_error("eth_apply_k_dot_static: n=%d needs %d blocks, the static scratch holds %d (n <= 2048)", n, q2_blocks(n),
-              ETH_NOALLOC_MAX_BLOCKS);
+    set_error("eth_apply_k_dot_static: n=%d needs %d element tiles, the static scratch holds %d (even n <= 2666)", n,
+              q2_blocks(n), ETH_NOALLOC_MAX_BLOCKS);
     return ETH_EINVAL;
   }
   NoAllocScratch* sc = nullptr;

@@ -195,6 +195,7 @@ eth_status tune_tiles(eth_grid* g, bool fp32) {
 extern "C" eth_status eth_grid_set_tile(eth_grid* g, int rows, int persistent) {
   using namespace eth;
   if (!g) { set_error("eth_grid_set_tile: NULL grid"); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   if (rows == 0) { g->tile_rows = 0; g->tuned = false; return ETH_OK; }
   if (!q2_tile_ok(rows)) { set_error("eth_grid_set_tile: rows=%d not in {4, 8, 16}", rows); return ETH_EINVAL; }
   if (persistent && rows != 8) { set_error("eth_grid_set_tile: the persistent kernel has 8 rows"); return ETH_EINVAL; }

@@ -267,17 +267,24 @@ __global__ void __launch_bounds__(Q2T) k_q2p(Q2Params<double, double, float> P, 
   }
 }
 
-// CTAs of the persistent launch: resident CTAs per SM x SMs, at most one per tile.
+// CTAs of the persistent launch on the current device: resident CTAs per SM x
+// SMs, at most one per tile (the occupancy figure is cached per device; the
+// shared-memory attribute is set on each device before its first launch).
 template <int F>
 int q2p_blocks(int n) {
-  static int cap = 0;
+  static SmemAttr attr;
+  static std::atomic<int> caps[ETH_MAX_DEVICES];
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const bool tracked = dev >= 0 && dev < ETH_MAX_DEVICES;
+  int cap = tracked ? caps[dev].load(std::memory_order_acquire) : 0;
   if (cap == 0) {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
+    int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaFuncSetAttribute(k_q2p<F>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)q2p_smem_bytes(F & QF_CONV));
+    smem_attr(k_q2p<F>, q2p_smem_bytes(F & QF_CONV), attr);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_q2p<F>, Q2T, q2p_smem_bytes(F & QF_CONV));
     cap = std::max(1, sms) * std::max(1, per);
+    if (tracked) caps[dev].store(cap, std::memory_order_release);
   }
   const int ntiles = (int)(cdiv(n, OEX) * cdiv(n, OEY));
   return std::min(ntiles, cap);

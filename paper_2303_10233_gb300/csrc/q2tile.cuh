@@ -597,13 +597,10 @@ inline int q2_blocks(int n, int ty = ETH_TEY) { return (int)(cdiv(n, OEX) * cdiv
 
 template <class TI, class TO, class CT, int F, int EPI, int TY = ETH_TEY>
 cudaError_t launch_q2(const Q2Params<TI, TO, CT>& P, cudaStream_t s) {
-  static bool attr_set = false;
+  static SmemAttr attr;
   const size_t smem = q2_smem_bytes(F, sizeof(CT), TY);
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_q2<TI, TO, CT, F, EPI, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  cudaError_t e = smem_attr(k_q2<TI, TO, CT, F, EPI, TY>, smem, attr);
+  if (e != cudaSuccess) return e;
   k_q2<TI, TO, CT, F, EPI, TY><<<q2_grid(P.n, TY), TEX * TY, smem, s>>>(P);
   return cudaGetLastError();
 }

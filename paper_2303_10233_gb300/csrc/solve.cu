@@ -987,6 +987,7 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   }
   if ((o.a_exact || o.mq_mode == ETH_MQ_EXACT) && !(o.inner_tol > 0)) { set_error("eth_solve: bad inner_tol"); return ETH_EINVAL; }
   if (o.precision != ETH_FP64 && o.precision != ETH_MIXED) { set_error("eth_solve: bad precision"); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   eth_stats st;
   std::memset(&st, 0, sizeof(st));
   Work* w;
@@ -1025,6 +1026,7 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
 eth_status eth_solve_host(eth_grid* g, const eth_opts* opts, const double* f, const double* ub, double* u, double* p,
                           eth_stats* stats) {
   if (!g || !f || !ub || !u || !p) { set_error("eth_solve_host: NULL argument"); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   Work* w;
   ETH_TRY(work_get(g, &w));
   const size_t nu2 = 2 * (size_t)g->nv, np = (size_t)g->n1 + g->n0;
@@ -1054,6 +1056,7 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
     set_error("eth_solve_adjoint: bad options");
     return ETH_EINVAL;
   }
+  ETH_ON_DEVICE(g);
   eth_stats st;
   std::memset(&st, 0, sizeof(st));
   Work* w;
@@ -1093,6 +1096,7 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
 
 eth_status eth_adjoint_gradients(eth_grid* g, const double* lu, const double* u, double* grad_f, double* grad_nu) {
   if (!g || !lu || !u || !grad_f || !grad_nu) { set_error("eth_adjoint_gradients: NULL argument"); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   Work* w;
   ETH_TRY(work_get(g, &w));
   StreamSwap guard(g, w);
@@ -1126,15 +1130,16 @@ eth_status eth_batch_solve(eth_batch* b, const eth_opts* opts, double* const* u,
   std::vector<eth_stats> ss(count);
   std::atomic<int> next{0};
   const int nw = std::max(1, std::min(count, b->workers > 0 ? b->workers : 16));
-  int dev = 0;
-  cudaGetDevice(&dev);
   // the autotuner times kernels: run it for every instance before the workers overlap them
   eth_opts o;
   if (opts) o = *opts; else eth_default_opts(&o);
   if (o.autotune)
-    for (int i : order) ETH_TRY(tune_tiles(b->grids[i], o.precision == ETH_MIXED));
-  auto worker = [&]() {
-    cudaSetDevice(dev);
+    for (int i : order) {
+      eth_grid* g = b->grids[i];
+      ETH_ON_DEVICE(g);
+      ETH_TRY(tune_tiles(g, o.precision == ETH_MIXED));
+    }
+  auto worker = [&]() {   // eth_solve makes each instance's device current
     while (true) {
       const int k = next.fetch_add(1);
       if (k >= count) break;
@@ -1168,6 +1173,7 @@ eth_status eth_picard(eth_grid* g, const eth_opts* opts, const double* f_nodal, 
   if (g->kind != ETH_OSEEN) { set_error("eth_picard: the grid must be created as ETH_OSEEN"); return ETH_EINVAL; }
   if (!g->has_coef) { set_error("eth_picard: call eth_set_coefficients first (viscosity)"); return ETH_EINVAL; }
   if (steps < 1) { set_error("eth_picard: steps=%d must be >= 1", steps); return ETH_EINVAL; }
+  ETH_ON_DEVICE(g);
   const size_t nu2 = 2 * (size_t)g->nv, np = (size_t)g->n1 + g->n0, nt = g->nt;
   const double nu = g->nu;
   ETH_CUDA(cudaMemsetAsync(u, 0, nu2 * 8, g->s));

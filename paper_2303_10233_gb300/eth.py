@@ -88,6 +88,7 @@ def load(path=LIB_PATH):
         "eth_est_infsup": (i, [vp, vp, vp, i, vp]),
         "eth_adjoint_gradients": (i, [vp, vp, vp, vp, ctypes.POINTER(d)]),
         "eth_apply_k_dot_static": (i, [i, d, d, d, d, d, i, vp, vp, vp, vp]),
+        "eth_apply_pcd": (i, [vp, i, i, i, i, vp, vp]),
         "eth_batch_create": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "eth_batch_solve": (i, [vp, ctypes.POINTER(Opts), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)]),
         "eth_batch_destroy": (None, [vp]),
@@ -130,12 +131,19 @@ def make_opts(**kw):
     return o
 
 
-def _ptr(t):
+def _ptr(t, numel=None, device=None):
+    """Device pointer of a contiguous CUDA float64 tensor; with ``numel`` its
+    length and with ``device`` its device are checked first (the C ABI takes raw
+    pointers and cannot check either)."""
     import torch
     if t is None:
         return None
     if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
         raise TypeError("expected a contiguous CUDA float64 tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"expected {numel} elements, got {t.numel()}")
+    if device is not None and t.device != device:
+        raise ValueError(f"tensor on {t.device}, the grid lives on {device}")
     return ctypes.c_void_p(t.data_ptr())
 
 
@@ -150,10 +158,16 @@ class Grid:
         self.nv, self.n1, self.n0, self.nt = sizes(self.n)
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if self.stream.device != self.device:
+            raise ValueError(f"stream of {self.stream.device} for a grid on {self.device}")
         h = ctypes.c_void_p()
-        _check(L.eth_grid_create(self.n, *map(float, domain), self.kind,
-                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        with torch.cuda.device(self.device):   # the handle belongs to the device current at creation
+            _check(L.eth_grid_create(self.n, *map(float, domain), self.kind,
+                                     ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self.h = h
+
+    def _p(self, t, numel):
+        return _ptr(t, numel, self.device)
 
     def close(self):
         if getattr(self, "h", None):
@@ -172,7 +186,7 @@ class Grid:
 
     def set_coefficients(self, nu, wind=None):
         self._wind = wind
-        _check(load().eth_set_coefficients(self.h, float(nu), _ptr(wind)))
+        _check(load().eth_set_coefficients(self.h, float(nu), self._p(wind, 2 * self.nv)))
 
     def set_tile(self, rows, persistent=False):
         """Pins the fused K apply's tile (32 x rows elements, rows in {4, 8, 16}; persistent form with
@@ -180,27 +194,39 @@ class Grid:
         _check(load().eth_grid_set_tile(self.h, int(rows), int(bool(persistent))))
 
     def set_rhs(self, f_nodal, ubc):
-        _check(load().eth_set_rhs(self.h, _ptr(f_nodal), _ptr(ubc)))
+        _check(load().eth_set_rhs(self.h, self._p(f_nodal, 2 * self.nv), self._p(ubc, 2 * self.nv)))
 
     def rhs(self):
         b = self._zeros(self.nt)
-        _check(load().eth_get_rhs(self.h, _ptr(b)))
+        _check(load().eth_get_rhs(self.h, self._p(b, self.nt)))
         return b
 
+    def _op_sizes(self, op):
+        u2, pp, u1 = 2 * self.nv, self.n1 + self.n0, 2 * self.nv + self.n1
+        return {"K": (self.nt, self.nt), "KT": (self.nt, self.nt), "A": (u2, u2), "F": (u2, u2), "MV": (u2, u2),
+                "B": (u2, pp), "BT": (pp, u2), "MQ": (pp, pp), "K1": (u1, u1), "K1T": (u1, u1)}[op]
+
     def apply(self, op, x, fp32=False):
-        out = {"K": self.nt, "KT": self.nt, "A": 2 * self.nv, "F": 2 * self.nv, "MV": 2 * self.nv,
-               "B": self.n1 + self.n0, "BT": 2 * self.nv, "MQ": self.n1 + self.n0,
-               "K1": 2 * self.nv + self.n1, "K1T": 2 * self.nv + self.n1}[op]
-        y = self._zeros(out)
-        _check(load().eth_apply(self.h, OPS[op], int(bool(fp32)), _ptr(x), _ptr(y)))
+        nin, nout = self._op_sizes(op)
+        y = self._zeros(nout)
+        _check(load().eth_apply(self.h, OPS[op], int(bool(fp32)), self._p(x, nin), self._p(y, nout)))
         return y
+
+    def apply_pcd(self, rp, cheb_steps=10, ap_its=2, adjoint=False, fp32=False):
+        """M_S^{-1} rp = Ap^+ F1 Q1^{-1} rp (the Q1 PCD Schur block of Step I) with the given
+        inner step counts; returns the mean-free result (N_1)."""
+        zp = self._zeros(self.n1)
+        _check(load().eth_apply_pcd(self.h, int(bool(adjoint)), int(bool(fp32)), int(cheb_steps), int(ap_its),
+                                    self._p(rp, self.n1), self._p(zp, self.n1)))
+        return zp
 
     def solve(self, u=None, p=None, **opts):
         u = self._zeros(2 * self.nv) if u is None else u
         p = self._zeros(self.n1 + self.n0) if p is None else p
         o = make_opts(**opts)
         st = Stats()
-        rc = load().eth_solve(self.h, ctypes.byref(o), _ptr(u), _ptr(p), ctypes.byref(st))
+        rc = load().eth_solve(self.h, ctypes.byref(o), self._p(u, 2 * self.nv), self._p(p, self.n1 + self.n0),
+                              ctypes.byref(st))
         if rc not in SOFT:
             _check(rc)
         return u, p, st.as_dict()
@@ -208,6 +234,8 @@ class Grid:
     def solve_host(self, f_nodal, ubc, **opts):
         f = np.ascontiguousarray(f_nodal, dtype=np.float64)
         ub = np.ascontiguousarray(ubc, dtype=np.float64)
+        if f.size != 2 * self.nv or ub.size != 2 * self.nv:
+            raise ValueError(f"expected host arrays of {2 * self.nv} elements")
         u = np.zeros(2 * self.nv); p = np.zeros(self.n1 + self.n0)
         o = make_opts(**opts)
         st = Stats()
@@ -219,6 +247,10 @@ class Grid:
 
     def solve_host_pinned(self, f_pinned, ubc_pinned, u_pinned, p_pinned, **opts):
         """eth_solve_host with caller-owned (pinned) host tensors; returns stats."""
+        for t, m in ((f_pinned, 2 * self.nv), (ubc_pinned, 2 * self.nv), (u_pinned, 2 * self.nv),
+                     (p_pinned, self.n1 + self.n0)):
+            if t.is_cuda or t.dtype != torch_float64() or not t.is_contiguous() or t.numel() != m:
+                raise ValueError(f"expected a contiguous host float64 tensor of {m} elements")
         o = make_opts(**opts)
         st = Stats()
         c = lambda t: ctypes.c_void_p(t.data_ptr())
@@ -232,7 +264,9 @@ class Grid:
         lu = self._zeros(2 * self.nv); lp = self._zeros(self.n1 + self.n0)
         o = make_opts(**opts)
         st = Stats()
-        rc = load().eth_solve_adjoint(self.h, ctypes.byref(o), _ptr(ru), _ptr(rp), _ptr(lu), _ptr(lp), ctypes.byref(st))
+        nu2, npp = 2 * self.nv, self.n1 + self.n0
+        rc = load().eth_solve_adjoint(self.h, ctypes.byref(o), self._p(ru, nu2), self._p(rp, npp), self._p(lu, nu2),
+                                      self._p(lp, npp), ctypes.byref(st))
         if rc not in SOFT:
             _check(rc)
         return lu, lp, st.as_dict()
@@ -245,8 +279,9 @@ class Grid:
         o = make_opts(**opts)
         res = (ctypes.c_double * steps)()
         st = (Stats * steps)()
-        rc = load().eth_picard(self.h, ctypes.byref(o), _ptr(f_nodal), _ptr(ubc), int(steps), _ptr(u), _ptr(p),
-                               res, st)
+        nu2 = 2 * self.nv
+        rc = load().eth_picard(self.h, ctypes.byref(o), self._p(f_nodal, nu2), self._p(ubc, nu2), int(steps),
+                               self._p(u, nu2), self._p(p, self.n1 + self.n0), res, st)
         if rc not in SOFT:
             _check(rc)
         return u, p, list(res), [s_.as_dict() for s_ in st]
@@ -259,31 +294,42 @@ class Grid:
         _check(load().eth_lanczos(self.h, 0, None, None, ctypes.byref(k)))
         d = torch.empty(k.value, dtype=torch.float64, device=self.device)
         gm = torch.empty(k.value, dtype=torch.float64, device=self.device)
-        _check(load().eth_lanczos(self.h, k.value, _ptr(d), _ptr(gm), ctypes.byref(k)))
+        _check(load().eth_lanczos(self.h, k.value, self._p(d, k.value), self._p(gm, k.value), ctypes.byref(k)))
         return d, gm
 
     def est_infsup(self, delta=None, gamma=None):
         """EST-MINRES estimates of gamma^2 after each MINRES iteration (NaN where none)."""
         if delta is None:
             delta, gamma = self.lanczos()
-        est = self._zeros(delta.numel())
-        _check(load().eth_est_infsup(self.h, _ptr(delta), _ptr(gamma), int(delta.numel()), _ptr(est)))
+        k = delta.numel()
+        est = self._zeros(k)
+        _check(load().eth_est_infsup(self.h, self._p(delta, k), self._p(gamma, k), int(k), self._p(est, k)))
         return est
 
     def adjoint_gradients(self, lu, u):
         """(grad_f, grad_nu) of J = ||u - u_t||^2 from the adjoint velocity lu."""
         gf = self._zeros(2 * self.nv)
         gn = ctypes.c_double()
-        _check(load().eth_adjoint_gradients(self.h, _ptr(lu), _ptr(u), _ptr(gf), ctypes.byref(gn)))
+        nu2 = 2 * self.nv
+        _check(load().eth_adjoint_gradients(self.h, self._p(lu, nu2), self._p(u, nu2), self._p(gf, nu2),
+                                            ctypes.byref(gn)))
         return gf, gn.value
 
 
 def apply_k_dot_static(n, nu, x, y, dot, fp32=False, domain=(-1.0, 1.0, -1.0, 1.0), stream=None):
     """y = K x and dot = <K x, x> for a Stokes grid, through the allocation-free entry point."""
     import torch
-    st = stream if stream is not None else torch.cuda.current_stream()
-    _check(load().eth_apply_k_dot_static(int(n), *map(float, domain), float(nu), int(bool(fp32)), _ptr(x), _ptr(y),
-                                         _ptr(dot), ctypes.c_void_p(st.cuda_stream)))
+    nt = sizes(int(n))[3]
+    dev = x.device
+    if dot.numel() < 1:
+        raise ValueError("dot needs one element")
+    px, py, pd = _ptr(x, nt, dev), _ptr(y, nt, dev), _ptr(dot, None, dev)
+    st = stream if stream is not None else torch.cuda.current_stream(dev)
+    if st.device != dev:
+        raise ValueError(f"stream of {st.device} for tensors on {dev}")
+    with torch.cuda.device(dev):   # the scratch address is looked up on the current device
+        _check(load().eth_apply_k_dot_static(int(n), *map(float, domain), float(nu), int(bool(fp32)), px, py, pd,
+                                             ctypes.c_void_p(st.cuda_stream)))
 
 
 class Batch:
@@ -297,6 +343,7 @@ class Batch:
         self.h = h
 
     def solve(self, **opts):
+        """Solves every instance; returns (velocities, pressures, stats per instance, status)."""
         us = [g._zeros(2 * g.nv) for g in self.grids]
         ps = [g._zeros(g.n1 + g.n0) for g in self.grids]
         ua = (ctypes.c_void_p * len(us))(*[t.data_ptr() for t in us])
@@ -316,6 +363,11 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def torch_float64():
+    import torch
+    return torch.float64
 
 
 def problem(w, device=None):

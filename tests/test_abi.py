@@ -65,3 +65,39 @@ def test_binding_structs_match_header(cname, pytype):
     """The ctypes mirrors of eth_opts / eth_stats list the header's fields in order."""
     ours = [f for f, _ in getattr(eth, pytype)._fields_]
     assert ours == _header_struct_fields(cname)
+
+
+class _FakeCuda:
+    """Stand-in for a CUDA float64 tensor (no GPU here): what the binding's checks read."""
+
+    def __init__(self, numel, device="cuda:0"):
+        import torch
+        self.is_cuda = True
+        self.dtype = torch.float64
+        self.device = torch.device(device)
+        self._n = numel
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._n
+
+    def data_ptr(self):
+        return 0
+
+
+def test_binding_checks_lengths_and_devices_before_the_call():
+    """The C ABI takes raw pointers and cannot check lengths: the binding must refuse a
+    short tensor or one on another device before calling into the library."""
+    import torch
+    nt = eth.sizes(16)[3]
+    assert eth._ptr(_FakeCuda(nt), nt, torch.device("cuda:0")) is not None
+    with pytest.raises(ValueError):
+        eth._ptr(_FakeCuda(nt - 1), nt, torch.device("cuda:0"))
+    with pytest.raises(ValueError):
+        eth._ptr(_FakeCuda(nt, "cuda:1"), nt, torch.device("cuda:0"))
+    with pytest.raises(TypeError):
+        eth._ptr(torch.zeros(nt, dtype=torch.float64))          # host tensor
+    with pytest.raises(ValueError):
+        eth.apply_k_dot_static(16, 1.0, _FakeCuda(nt - 5), _FakeCuda(nt), _FakeCuda(1))

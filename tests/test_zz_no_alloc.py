@@ -45,6 +45,14 @@ def test_static_scratch_apply_matches_handle_apply(eth, n, fp32):
 
 
 def test_static_scratch_rejects_oversize(eth):
+    """Through the C ABI directly: n = 4096 needs more element tiles than the static
+    scratch holds, and the entry point refuses it before touching the buffers."""
+    import ctypes
     x = torch.zeros(1, dtype=torch.float64, device="cuda")
-    with pytest.raises(eth.EthError):
-        eth.apply_k_dot_static(4096, 1.0, x, x, x)
+    p = ctypes.c_void_p(x.data_ptr())
+    L = eth.load()
+    rc = L.eth_apply_k_dot_static(4096, -1.0, 1.0, -1.0, 1.0, 1.0, 0, p, p, p,
+                                  ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 1 and b"static scratch" in L.eth_last_error()
+    with pytest.raises(ValueError):   # the Python wrapper checks the tensor length first
+        eth.apply_k_dot_static(16, 1.0, x, x, x)
