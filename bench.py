@@ -14,7 +14,9 @@ The L2 cache (126 MB) is flushed between steps by writing a 512 MB buffer,
 outside the per-step CUDA-event timing.
 
 ``--impl reference`` times the FP64 CPU oracle (SciPy, exact-block MINRES)
-on a bounded number of iterations of the same workload.
+on a bounded number of iterations of the same workload.  The default run also
+reports the oracle's whole solve to tolerance (cpu_baseline), the Oseen 512^2
+two-stage solve (oseen512) and the roofline of the K apply (roofline).
 """
 from __future__ import annotations
 
@@ -29,10 +31,11 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
-# the oracle (CPU baseline / reference arm) is reported as one core: keep its BLAS
-# single-threaded (set before numpy is imported; the GPU path uses no CPU BLAS)
+# the oracle (CPU baseline / reference arm) may use every host core for its dense
+# BLAS work (set before numpy is imported; the GPU path uses no CPU BLAS); its sparse
+# products and SuperLU solves run on one core whatever this setting
 for _v in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
-    os.environ.setdefault(_v, "1")
+    os.environ.setdefault(_v, str(os.cpu_count() or 1))
 
 N_GRID = 256
 SEED = 0
@@ -111,6 +114,42 @@ def _peaks():
 # ---------------------------------------------------------------------------
 # oracle (CPU) sample: exact-block MINRES iterations on the same workload
 # ---------------------------------------------------------------------------
+def host_info():
+    """Host cores and the CPU model line of lscpu (recorded beside the CPU figures)."""
+    info = {"os_cpu_count": os.cpu_count(), "blas_threads": os.environ.get("OPENBLAS_NUM_THREADS")}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            k, _, v = ln.partition(":")
+            if k.strip() in ("Model name", "Architecture", "CPU(s)", "Thread(s) per core", "Socket(s)"):
+                info[k.strip()] = v.strip()
+    except Exception:
+        pass
+    return info
+
+
+def oracle_to_tolerance(n, tol):
+    """The oracle's time to tolerance on the bench workload: Algorithm 1 MINRES with the
+    exact P_1 blocks (SuperLU factorisations, timed separately) from the lifted zero
+    guess until the true relative residual is <= tol."""
+    import numpy as np
+    from oracle import fem, krylov, problem
+    from paper_2303_10233_gb300 import workloads as W
+    w = W.mms(n, seed=SEED)
+    g = fem.Grid(n)
+    s = problem.System(g, w["nu"], w["wind"])
+    b = s.rhs(w["f_nodal"], w["ubc"])
+    t = time.perf_counter()
+    P = krylov.P1(s)
+    tfac = time.perf_counter() - t
+    x0 = np.concatenate([s.DB @ b[: g.nu], np.zeros(g.np_)])
+    t = time.perf_counter()
+    x, info = krylov.minres(lambda v: s.K @ v, P, b, x0, tol=tol, maxit=400, true_tol=tol)
+    dt = time.perf_counter() - t
+    res = float(np.linalg.norm(b - s.K @ x) / np.linalg.norm(b))
+    return info["its"], dt, tfac, res
+
+
 def oracle_sample(n, iters, setup=None):
     import numpy as np
     from oracle import fem, krylov, problem
@@ -164,7 +203,8 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": _config(nt, ws),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                             "host": host_info()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -271,6 +311,9 @@ def run_ours(args):
     h2d = 2 * nu2 * 8
     d2h = nt * 8
 
+    # ---- Oseen 512^2 (two-stage PCD GMRES, nu = 1/100): time to tolerance, mixed and FP64
+    oseen = oseen_line(torch, eth, W, local)
+
     # ---- roofline of the dominant kernel, timed live on the launching stream
     roof = roofline(G, torch, eth)
     clocks = clk.stop()
@@ -279,12 +322,14 @@ def run_ours(args):
         return
     cpu = None
     if ws == 1 and not args.no_cpu:
-        its_c, dt_c, setup = oracle_sample(N_GRID, 2)
-        m = max(2, min(30, int(15.0 / max(dt_c / max(its_c, 1), 1e-3))))
-        its_c, dt_c, _ = oracle_sample(N_GRID, m, setup)
+        its_c, dt_c, tfac, res_c = oracle_to_tolerance(N_GRID, TOL)
         cpu = {"value": nt * its_c / dt_c / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{its_c} exact-block MINRES iterations of the 256^2 MMS system in {dt_c:.1f} s "
-                         f"(SuperLU factorisation {setup[4]:.1f} s excluded); SciPy sparse, single-threaded"}
+               "time_to_tol_s": dt_c, "factorisation_s": tfac, "iters": its_c, "relres": res_c,
+               "host": host_info(),
+               "sample": f"the whole 256^2 MMS solve: {its_c} exact-block MINRES iterations (Algorithm 1, P_1 by "
+                         f"SuperLU) to relative residual {res_c:.1e} in {dt_c:.1f} s, factorisation {tfac:.1f} s "
+                         f"not included; SciPy sparse products and SuperLU solves use one core (BLAS threads = "
+                         f"host cores)"}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
@@ -299,6 +344,7 @@ def run_ours(args):
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "roofline": roof,
+        "oseen512": oseen,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "wall_s": t_wall,
@@ -310,74 +356,143 @@ def run_ours(args):
 
 
 def _kernel_hash():
-    """Hash of the sources of the roofline kernel, the plain fused K apply (the tile
-    kernel and the helpers it uses; the reduction finishers it does not use are left out)."""
+    """Hash of the sources of the roofline kernel, the warp-strip fused K apply (its
+    header, the element helpers of the tile header and the conversions of common.cuh)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("q2tile.cuh", "common.cuh"):
+    for f in ("q2strip.cuh", "q2tile.cuh", "common.cuh"):
         with open(os.path.join(ROOT, "paper_2303_10233_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _profiled_traffic():
+def _profiled_traffic(rows):
     """DRAM bytes per launch of the roofline kernel from the committed ncu summary,
-    or None when the kernel sources changed since that capture."""
-    path = os.path.join(ROOT, "profiles", "kapply_stokes_1024_fp32.txt")
+    or None when the kernel sources changed since that capture or it was taken with
+    another number of element rows per warp."""
+    path = os.path.join(ROOT, "profiles", "kapply_strip_stokes_1024_fp32.txt")
     try:
         kv = dict(line.split("=", 1) for line in open(path).read().split("\n") if "=" in line)
         if kv.get("kernel_source_hash", "").strip() != _kernel_hash():
+            return None
+        if int(kv.get("rows", "0")) != rows:
             return None
         return float(kv["dram_bytes_read"]) + float(kv["dram_bytes_write"])
     except Exception:
         return None
 
 
-def roofline(G, torch, eth):
-    """Fused K apply (FP32 element arithmetic, FP64 in/out) on the 1024^2 grid of the
-    same workload family; two input/output pairs alternate so the 336 MB working set
-    exceeds L2.  Algorithmic bytes = 16 B x N_t per launch (FP64 in + out)."""
-    from paper_2303_10233_gb300 import workloads as W
-    peak, src = _peaks()
-    n = 1024
-    w = W.mms(n, seed=SEED)
-    H = eth.problem(w, device=G.device.index)
-    xs = [torch.randn(H.nt, dtype=torch.float64, device=G.device) for _ in range(2)]
+def oseen_line(torch, eth, W, dev, steps=3):
+    """The Oseen workload on 512^2 (seeded wind, nu = 1/100, lid-driven cavity): median
+    CUDA-event time to a 1e-6 true residual of the mixed-precision two-stage PCD solve
+    (GMRES(50), adaptive restart to 160) and of the plain FP64 form, iterations of both
+    stages, and N_t x iterations / time."""
+    w = W.oseen_cavity(512, nu=0.01, seed=1)
+    O = eth.problem(w, device=dev)
+    opts = dict(tol=TOL, restart_max=160, maxit=4000)
+    out = {"workload": "oseen_cavity_512_nu0.01", "N_t": O.nt}
+    for prec in ("mixed", "fp64"):
+        O.solve(precision=prec, **opts)
+        ms, sts = [], []
+        for _ in range(steps if prec == "mixed" else 2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, _, st = O.solve(precision=prec, **opts)
+            e1.record()
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            sts.append(st)
+        its = sts[-1]["iters_total"]
+        t = statistics.median(ms)
+        out[prec] = {"ms": t, "iters": [sts[-1]["iters_stage1"], sts[-1]["iters_stage2"]],
+                     "relres": max(x["relres_true"] for x in sts), "status": sts[-1]["status"],
+                     "mdof_iter_s": O.nt * its / (t / 1e3) / 1e6}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
+    O.close()
+    return out
+
+
+def _time_apply(torch, eth, H, fp32, reps=40):
+    """CUDA-event time (s) of one eth_apply(K) on H's stream, two input/output pairs
+    alternating (their 336 MB at 1024^2 exceed the L2)."""
+    xs = [torch.randn(H.nt, dtype=torch.float64, device=H.device) for _ in range(2)]
     ys = [torch.empty_like(xs[0]) for _ in range(2)]
     L = eth.load()
     for k in range(4):
-        L.eth_apply(H.h, eth.OPS["K"], 1, eth._ptr(xs[k % 2]), eth._ptr(ys[k % 2]))
+        L.eth_apply(H.h, eth.OPS["K"], fp32, eth._ptr(xs[k % 2]), eth._ptr(ys[k % 2]))
     torch.cuda.synchronize()
-    reps = 40
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for k in range(reps):
-        L.eth_apply(H.h, eth.OPS["K"], 1, eth._ptr(xs[k % 2]), eth._ptr(ys[k % 2]))
-    e1.record()
+    with torch.cuda.stream(H.stream):
+        e0.record()
+        for k in range(reps):
+            L.eth_apply(H.h, eth.OPS["K"], fp32, eth._ptr(xs[k % 2]), eth._ptr(ys[k % 2]))
+        e1.record()
     torch.cuda.synchronize()
-    t = e0.elapsed_time(e1) / reps / 1e3
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+ROOF_ROWS = (2, 4, 8)   # warp-strip shapes timed; the fastest is the roofline kernel
+
+
+def roofline(G, torch, eth):
+    """Fused K apply (warp-strip kernel k_q2s, FP32 element arithmetic, FP64 in/out) on
+    the 1024^2 grid of the same workload family, timed live for each element-row count
+    per warp in ROOF_ROWS; the fastest is reported.  Algorithmic bytes = 16 B x N_t per
+    launch (FP64 in + out).  The shared-memory tile kernel of the same operator is
+    timed beside it, and the Oseen operator (its FP32 wind read as well: + 8 B x N_v) on
+    the 512^2 grid of the Oseen workload."""
+    from paper_2303_10233_gb300 import workloads as W
+    peak, src = _peaks()
+    H = eth.problem(W.mms(1024, seed=SEED), device=G.device.index)
+    times = {}
+    for rows in ROOF_ROWS:
+        H.set_tile(rows, 2)
+        times[rows] = _time_apply(torch, eth, H, 1)
+    H.set_tile(8, 0)
+    t_tile = _time_apply(torch, eth, H, 1)
+    rows = min(times, key=times.get)
+    t = times[rows]
     bytes_ = 16.0 * H.nt
     ach = bytes_ / t / 1e9
     H.close()
-    return {"kernel": "k_q2 fused K apply (FP32 element math, FP64 I/O), Stokes n=1024", "bound": "hbm",
+    O = eth.problem(W.oseen_cavity(512, nu=0.01, seed=1), device=G.device.index)
+    osn = {}
+    for r in ROOF_ROWS:
+        O.set_tile(r, 2)
+        osn[f"strip{r}"] = _time_apply(torch, eth, O, 1)
+    O.set_tile(8, 0)
+    osn["tile32x8"] = _time_apply(torch, eth, O, 1)
+    best = min(osn, key=osn.get)
+    ob = 16.0 * O.nt + 8.0 * O.nv
+    O.close()
+    return {"kernel": f"k_q2s warp-strip fused K apply, {rows} element rows per warp (FP32 element math, "
+                      f"FP64 I/O), Stokes n=1024", "bound": "hbm",
             "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-            "peak_source": f"{src} (burst copy)", "traffic": _profiled_traffic(),
-            "alg_bytes_per_launch": bytes_, "us_per_launch": t * 1e6}
+            "peak_source": f"{src} (burst copy)", "traffic": _profiled_traffic(rows),
+            "alg_bytes_per_launch": bytes_, "us_per_launch": t * 1e6,
+            "us_by_rows": {str(r): round(v * 1e6, 2) for r, v in times.items()},
+            "tile_kernel_us": t_tile * 1e6, "tile_kernel_frac": bytes_ / t_tile / 1e9 / peak,
+            "oseen512": {"best": best, "us": osn[best] * 1e6, "alg_bytes_per_launch": ob,
+                         "achieved_gbs": ob / osn[best] / 1e9, "frac": ob / osn[best] / 1e9 / peak,
+                         "us_by_kernel": {k: round(v * 1e6, 2) for k, v in osn.items()}}}
 
 
-def profile_apply(n, kind):
+def profile_apply(n, kind, rows):
+    """Five K applies (FP32 element arithmetic) on an n x n grid for ncu captures: the
+    warp-strip kernel with `rows` element rows per warp, or the 32 x 8 tile kernel (rows 0)."""
     import torch
     import __graft_entry__ as ge
     ge.build()
     from paper_2303_10233_gb300 import eth, workloads as W
     w = W.oseen_cavity(n, nu=0.01, seed=1) if kind == "oseen" else W.mms(n, seed=SEED)
     G = eth.problem(w)
+    G.set_tile(rows, 2) if rows else G.set_tile(8, 0)
     x = torch.randn(G.nt, dtype=torch.float64, device="cuda")
     y = torch.empty_like(x)
     for _ in range(5):
         eth.load().eth_apply(G.h, eth.OPS["K"], 1, eth._ptr(x), eth._ptr(y))
     torch.cuda.synchronize()
-    print(f"profile_apply n={n} kind={kind} N_t={G.nt} done")
+    print(f"profile_apply n={n} kind={kind} rows={rows} N_t={G.nt} done")
     G.close()
 
 
@@ -441,6 +556,8 @@ def main():
     ap.add_argument("--profile-apply", type=int, default=0, metavar="N",
                     help="only run the fused K apply (FP32 math) 5 times on an N x N grid (for ncu captures)")
     ap.add_argument("--profile-kind", default="stokes", choices=["stokes", "oseen"])
+    ap.add_argument("--profile-rows", type=int, default=4,
+                    help="element rows per warp of the strip kernel in --profile-apply (0: the tile kernel)")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="N",
                     help="only run two default solves on an N x N grid of --profile-kind (for ncu launch lists)")
     ap.add_argument("--est", type=int, default=0, metavar="N",
@@ -450,7 +567,7 @@ def main():
         est_table(args.est)
         return
     if args.profile_apply:
-        profile_apply(args.profile_apply, args.profile_kind)
+        profile_apply(args.profile_apply, args.profile_kind, args.profile_rows)
         return
     if args.profile_solve:
         profile_solve(args.profile_solve, args.profile_kind)

@@ -100,12 +100,14 @@ typedef struct {
   int verbose;
   int autotune;            /* 1: before the first solve of a grid, time the
                               fused K apply with tiles of 32 x {4, 8, 16}
-                              elements per CTA and the persistent 32 x 8 form
-                              (mixed precision) and keep the fastest (cached
+                              elements per CTA, the persistent 32 x 8 form
+                              (mixed precision) and the warp-strip form with
+                              {2, 4, 8, 16} element rows per warp, and keep
+                              the fastest (cached
                               per grid size, operator and precision for the
                               process), and for GMRES the basis vectors per
-                              Gram-Schmidt pass in {4, 8, 16}; 0: 32 x 8, one
-                              tile per CTA, 16 vectors per pass              */
+                              Gram-Schmidt pass in {4, 8, 16}; 0: warp strips
+                              of 8 element rows, 16 vectors per pass         */
   int restart_max;         /* GMRES: when a restart cycle reduces the FP64
                               residual by less than a factor 2, the next
                               cycles use twice the restart length, up to
@@ -128,7 +130,9 @@ typedef struct {
                               because the FP64 residual had grown (0 or 1 per
                               stage)                                         */
   int tile_rows;           /* element rows per tile of the fused K apply used */
-  int tile_persistent;     /* 1: its persistent pipelined form was used       */
+  int tile_persistent;     /* 1: its persistent pipelined form was used;
+                              2: the warp-strip form (tile_rows element rows
+                              per warp)                                      */
 } eth_stats;
 
 /* Sizes of an n x n grid: N_v = (2n+1)^2, N_1 = (n+1)^2, N_0 = n^2.
@@ -146,10 +150,13 @@ eth_status eth_grid_create(int n, double x0, double x1, double y0, double y1,
 void eth_grid_destroy(eth_grid* g);
 
 /* Pins the tile of the fused K apply: 32 x rows elements per CTA, rows in
- * {4, 8, 16}, one tile per CTA; or, with persistent != 0 (rows = 8), a grid of
+ * {4, 8, 16}, one tile per CTA; or, with persistent = 1 (rows = 8), a grid of
  * resident CTAs that walk over the tiles and copy the next tile's input
  * (cp.async) while computing the current one (FP32 element arithmetic only;
- * FP64 applies use 32 x 8 one tile per CTA).  Turns the autotuner off for this
+ * FP64 applies use 32 x 8 one tile per CTA); or, with persistent = 2, the
+ * warp-strip form (the default): each warp walks `rows` element rows (2, 4, 8,
+ * 16 or 32) of a strip of 30 element columns, keeping the shared node row in
+ * registers (FP32 or FP64 element arithmetic).  Turns the autotuner off for this
  * grid; rows = 0 restores the default and lets the next solve with
  * opts.autotune tune again.  Every apply gives bitwise the same K x whatever
  * the tile (each node sums its element contributions in one fixed order);

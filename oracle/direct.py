@@ -8,6 +8,13 @@ The enclosed-flow system K is singular with null space span{e1, e0}
 
 is nonsingular, and for a consistent b it returns the solution with
 sum(p1) = sum(p0) = 0 and l = 0.  SuperLU in float64.
+
+The bordered matrix has dense border rows and columns, which makes the sparse
+factorisation slow beyond n = 64.  ``solve_pinned`` computes the same solution
+another way for larger grids: it fixes one Q1 and one P0 pressure value at zero
+(identity rows and zero columns for those two unknowns, a nonsingular sparse
+system when b is consistent) and then removes the e1 / e0 components, which
+gives the same canonical representative.
 """
 from __future__ import annotations
 
@@ -38,3 +45,15 @@ def solve_transpose(sys, b):
     E = np.stack([sys.e1, sys.e0], axis=1)
     x, lam = bordered_solve(sys.K.T.tocsr(), E, b)
     return x, lam
+
+
+def solve_pinned(sys, b):
+    """Exact canonical solution via two pinned pressure unknowns (see the module
+    docstring); b must be consistent (zero e1 / e0 components)."""
+    g = sys.g
+    keep = np.ones(sys.K.shape[0])
+    keep[[g.nu, g.nu + g.n1]] = 0.0          # first Q1 and first P0 pressure
+    Dk = sp.diags(keep)
+    Kp = (Dk @ sys.K @ Dk + sp.diags(1.0 - keep)).tocsc()
+    x = spla.splu(Kp, permc_spec="COLAMD").solve(b * keep)
+    return sys.canonical(x)

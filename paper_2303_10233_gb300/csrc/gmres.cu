@@ -392,27 +392,64 @@ __global__ void k_pcg_dot(int m, const T* __restrict__ a, const T* __restrict__ 
   multi_finish(1, gridDim.x, part, ticket, out);
 }
 
-// x += alpha p ; r -= alpha q   (alpha = rz / pAp)
+// (<r, z>, sum z) -> out[0], out[1]: the PCG inner product and the constant
+// component of the preconditioned residual (the Q1 V-cycle of a singular operator
+// may return one; it is removed from the search direction below)
+template <class T>
+__global__ void k_pcg_dot_sum(int m, const T* __restrict__ r, const T* __restrict__ z, double* part, unsigned* ticket,
+                              double* out, const int* done) {
+  ETH_GRID_DEP_WAIT();
+  if (done && *done) return;
+  double a = 0.0, c = 0.0;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
+    const double zk = (double)z[k];
+    a += (double)r[k] * zk;
+    c += zk;
+  }
+  double v[2] = {a, c};
+  block_sum<2>(v);
+  if (threadIdx.x == 0) { part[blockIdx.x] = v[0]; part[gridDim.x + blockIdx.x] = v[1]; }
+  multi_finish(2, gridDim.x, part, ticket, out);
+}
+
+// p = z - mean(z)   (first PCG direction, mean from gs->pcg[1]); keeps the initial
+// <r, z> in gs->pcg[6] for the convergence guard of k_pcg_xr
+template <class T>
+__global__ void k_pcg_p0(int m, const T* __restrict__ z, T* __restrict__ p, GScalars* gs, const int* done) {
+  ETH_GRID_DEP_WAIT();
+  if (done && *done) return;
+  const T mu = (T)(gs->pcg[1] / m);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) p[k] = z[k] - mu;
+  if (blockIdx.x == 0 && threadIdx.x == 0) gs->pcg[6] = gs->pcg[0];
+}
+
+// x += alpha p ; r -= alpha q   (alpha = rz / pAp).  Once <r, z> has fallen to the
+// rounding level of T relative to its initial value the iterate is left alone:
+// further steps of a converged CG on the singular Ap only amplify rounding noise.
 template <class T>
 __global__ void k_pcg_xr(int m, const T* __restrict__ p, const T* __restrict__ q, T* __restrict__ x, T* __restrict__ r,
                          const GScalars* gs, const int* done) {
   ETH_GRID_DEP_WAIT();
   if (done && *done) return;
-  const double pap = gs->pcg[1];
-  const T a = (T)(pap != 0.0 ? gs->pcg[0] / pap : 0.0);   // zero right-hand side: stay at zero
+  const double pap = gs->pcg[1], rz = gs->pcg[0];
+  const double floor_rz = (sizeof(T) == 4 ? 1e-13 : 1e-28) * gs->pcg[6];
+  const T a = (T)((pap > 0.0 && rz > floor_rz) ? rz / pap : 0.0);   // zero right-hand side: stay at zero
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) {
     x[k] += a * p[k];
     r[k] -= a * q[k];
   }
 }
 
-// p = z + (rz_new / rz) p ; rz = rz_new
+// p = (z - mean z) + (rz_new / rz) p ; rz = rz_new   (rz_new in gs->pcg[2], sum z in gs->pcg[3]).
+// Keeping p free of constants keeps the iterate's constant component from drifting
+// when many steps run on the singular Ap.
 template <class T>
 __global__ void k_pcg_p(int m, const T* __restrict__ z, T* __restrict__ p, GScalars* gs, const int* done) {
   ETH_GRID_DEP_WAIT();
   if (done && *done) return;
   const T bt = (T)(gs->pcg[0] != 0.0 ? gs->pcg[2] / gs->pcg[0] : 0.0);
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) p[k] = z[k] + bt * p[k];
+  const T mu = (T)(gs->pcg[3] / m);
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) p[k] = (z[k] - mu) + bt * p[k];
   __syncthreads();
 }
 __global__ void k_pcg_shift(GScalars* gs) {
@@ -644,8 +681,8 @@ static eth_status ap_solve(eth_grid* g, Work* w, const T* b, T* x, int its, cons
   ETH_CUDA(cudaGetLastError());
   g->launches += 3;
   ETH_TRY(q1_vcycle<T>(g, w, r, z, done));
-  k_copy_t<T><<<gb(m), 256, 0, g->s>>>(m, z, p);
-  k_pcg_dot<T><<<gb(m), 256, 0, g->s>>>(m, r, z, G->part, G->ticket + 1, &G->gs->pcg[0], done);
+  k_pcg_dot_sum<T><<<gb(m), 256, 0, g->s>>>(m, r, z, G->part, G->ticket + 1, &G->gs->pcg[0], done);
+  k_pcg_p0<T><<<gb(m), 256, 0, g->s>>>(m, z, p, G->gs, done);
   ETH_CUDA(cudaGetLastError());
   g->launches += 2;
   for (int it = 0; it < its; ++it) {
@@ -655,7 +692,7 @@ static eth_status ap_solve(eth_grid* g, Work* w, const T* b, T* x, int its, cons
     g->launches++;
     if (it + 1 == its) break;
     ETH_TRY(q1_vcycle<T>(g, w, r, z, done));
-    k_pcg_dot<T><<<gb(m), 256, 0, g->s>>>(m, r, z, G->part, G->ticket + 1, &G->gs->pcg[2], done);
+    k_pcg_dot_sum<T><<<gb(m), 256, 0, g->s>>>(m, r, z, G->part, G->ticket + 1, &G->gs->pcg[2], done);
     k_pcg_p<T><<<gb(m), 256, 0, g->s>>>(m, z, p, G->gs, done);
     k_pcg_shift<<<1, 1, 0, g->s>>>(G->gs);
     ETH_CUDA(cudaGetLastError());

@@ -28,9 +28,10 @@ const double* wind_ptr<double>(eth_grid* g) { return g->wind; }
 // TUNED: the fused K apply, launched with the grid's (autotuned) tile: 32 x rows
 // elements, one tile per CTA, or (FP32 element arithmetic only) the persistent
 // pipelined 32 x 8 kernel.  A tile code is rows, or rows + TILE_PERSIST.
-int tile_code(const eth_grid* g) { return g->tile_rows ? g->tile_rows : ETH_TEY; }
+int tile_code(const eth_grid* g) { return g->tile_rows ? g->tile_rows : TILE_STRIP + 8; }
 int tile_rows(const eth_grid* g) { return tile_code(g) % TILE_PERSIST; }
-bool tile_persistent(const eth_grid* g) { return tile_code(g) >= TILE_PERSIST; }
+bool tile_persistent(const eth_grid* g) { return tile_code(g) >= TILE_PERSIST && tile_code(g) < TILE_STRIP; }
+bool tile_strip(const eth_grid* g) { return tile_code(g) >= TILE_STRIP; }
 
 template <class CT, int F, bool TUNED = false>
 static eth_status run_q2(eth_grid* g, const double* x, const double* p, double* y, double* yp,
@@ -43,6 +44,15 @@ static eth_status run_q2(eth_grid* g, const double* x, const double* p, double* 
   if (TUNED) {
     if (!code) code = tile_code(g);
     const int ty = code % TILE_PERSIST;
+    if constexpr ((F & QF_XIN) && (F & QF_UOUT) && !(F & (QF_NOBC | QF_MASS))) {
+      if (code >= TILE_STRIP) {
+        const int rows = code - TILE_STRIP;
+        if (slot) P.slot.total = q2s_blocks(g->n, rows);
+        ETH_CUDA((launch_q2s<CT, F>(P, g->s, rows)));
+        g->launches++;
+        return ETH_OK;
+      }
+    }
     if constexpr (sizeof(CT) == 4 && (F & QF_XIN) && !(F & (QF_NOBC | QF_MASS))) {
       if (code >= TILE_PERSIST) {
         if (slot) P.slot.total = q2p_blocks<F>(g->n);
@@ -69,14 +79,14 @@ static eth_status apply_t(eth_grid* g, eth_op op, const double* x, double* y) {
       if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
       return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
     case ETH_OP_KT:
-      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
-      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
     case ETH_OP_K1:
-      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
-      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
     case ETH_OP_K1T:
-      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
-      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2);
+      if (conv) return run_q2<CT, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
+      return run_q2<CT, QF_DIFF | QF_XIN | QF_PIN | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2);
     case ETH_OP_A:
       return run_q2<CT, QF_DIFF | QF_XIN | QF_UOUT>(g, x, nullptr, y, nullptr);
     case ETH_OP_F:
@@ -133,9 +143,9 @@ eth_status op_apply_K(eth_grid* g, bool fp32, bool trans, const double* x, doubl
     if (conv) return run_q2<float, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2, done);
     return run_q2<float, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2, done);
   }
-  if (conv && trans) return run_q2<double, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
-  if (conv) return run_q2<double, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
-  return run_q2<double, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT>(g, x, x + nu2, y, y + nu2, done);
+  if (conv && trans) return run_q2<double, QF_DIFF | QF_CONV | QF_TRANS | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2, done);
+  if (conv) return run_q2<double, QF_DIFF | QF_CONV | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2, done);
+  return run_q2<double, QF_DIFF | QF_XIN | QF_PIN | QF_P0 | QF_UOUT | QF_POUT, true>(g, x, x + nu2, y, y + nu2, done);
 }
 
 // ---------------------------------------------------------------------------
@@ -160,13 +170,14 @@ eth_status tune_tiles(eth_grid* g, bool fp32) {
   cudaEvent_t e0, e1;
   ETH_CUDA(cudaEventCreate(&e0));
   ETH_CUDA(cudaEventCreate(&e1));
-  int best = ETH_TEY;
+  int best = TILE_STRIP + 8;
   float best_ms = 1e30f;
   eth_status st = ETH_OK;
-  const int cands[4] = {4, 8, 16, 8 + TILE_PERSIST};
+  const int cands[8] = {4, 8, 16, 8 + TILE_PERSIST, 2 + TILE_STRIP, 4 + TILE_STRIP, 8 + TILE_STRIP, 16 + TILE_STRIP};
   for (int ty : cands) {
-    if (ty >= TILE_PERSIST && !fp32) continue;
+    if (ty >= TILE_PERSIST && ty < TILE_STRIP && !fp32) continue;
     if (ty < TILE_PERSIST && q2_blocks(g->n, ty) > g->part_cap) continue;
+    if (ty >= TILE_STRIP && q2s_blocks(g->n, ty - TILE_STRIP) > g->part_cap) continue;
     Slot s = make_slot(g, 11, 0);
     for (int r = 0; r < 2 && st == ETH_OK; ++r) st = op_apply_tiles(g, fp32, g->b, g->tmp, s, ty);
     if (st != ETH_OK) break;
@@ -197,6 +208,13 @@ extern "C" eth_status eth_grid_set_tile(eth_grid* g, int rows, int persistent) {
   if (!g) { set_error("eth_grid_set_tile: NULL grid"); return ETH_EINVAL; }
   ETH_ON_DEVICE(g);
   if (rows == 0) { g->tile_rows = 0; g->tuned = false; return ETH_OK; }
+  if (persistent == 2) {   // warp-strip kernel, `rows` element rows per warp
+    if (!q2s_rows_ok(rows)) { set_error("eth_grid_set_tile: strip rows=%d not in {2, 4, 8, 16, 32}", rows); return ETH_EINVAL; }
+    if (q2s_blocks(g->n, rows) > g->part_cap) { set_error("eth_grid_set_tile: too many strips for n=%d", g->n); return ETH_EINVAL; }
+    g->tile_rows = rows + TILE_STRIP;
+    g->tuned = true;
+    return ETH_OK;
+  }
   if (!q2_tile_ok(rows)) { set_error("eth_grid_set_tile: rows=%d not in {4, 8, 16}", rows); return ETH_EINVAL; }
   if (persistent && rows != 8) { set_error("eth_grid_set_tile: the persistent kernel has 8 rows"); return ETH_EINVAL; }
   if (!persistent && q2_blocks(g->n, rows) > g->part_cap) { set_error("eth_grid_set_tile: too many tiles for n=%d", g->n); return ETH_EINVAL; }

@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(Q2T) k_q2p(Q2Params<double, double, float> P, 
 // SMs, at most one per tile (the occupancy figure is cached per device; the
 // shared-memory attribute is set on each device before its first launch).
 template <int F>
-int q2p_blocks(int n) {
+static int q2p_blocks(int n) {   // per translation unit, like launch_q2
   static SmemAttr attr;
   static std::atomic<int> caps[ETH_MAX_DEVICES];
   int dev = 0;
@@ -291,7 +291,7 @@ int q2p_blocks(int n) {
 }
 
 template <int F>
-cudaError_t launch_q2p(const Q2Params<double, double, float>& P, cudaStream_t s) {
+static cudaError_t launch_q2p(const Q2Params<double, double, float>& P, cudaStream_t s) {
   const int grid = q2p_blocks<F>(P.n);   // also sets the shared-memory attribute
   const int ntx = (int)cdiv(P.n, OEX), ntiles = ntx * (int)cdiv(P.n, OEY);
   k_q2p<F><<<grid, Q2T, q2p_smem_bytes(F & QF_CONV), s>>>(P, ntx, ntiles);

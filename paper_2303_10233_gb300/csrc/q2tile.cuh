@@ -595,8 +595,11 @@ inline size_t q2_smem_bytes(int F, size_t ct_size, int ty = ETH_TEY) {
 inline dim3 q2_grid(int n, int ty = ETH_TEY) { return dim3(cdiv(n, OEX), cdiv(n, ty - 1)); }
 inline int q2_blocks(int n, int ty = ETH_TEY) { return (int)(cdiv(n, OEX) * cdiv(n, ty - 1)); }
 
+// Kernel stubs have internal linkage in every translation unit (each unit launches
+// its own copy of a kernel), so the launcher and its record of the shared-memory
+// attribute are per translation unit too (static).
 template <class TI, class TO, class CT, int F, int EPI, int TY = ETH_TEY>
-cudaError_t launch_q2(const Q2Params<TI, TO, CT>& P, cudaStream_t s) {
+static cudaError_t launch_q2(const Q2Params<TI, TO, CT>& P, cudaStream_t s) {
   static SmemAttr attr;
   const size_t smem = q2_smem_bytes(F, sizeof(CT), TY);
   cudaError_t e = smem_attr(k_q2<TI, TO, CT, F, EPI, TY>, smem, attr);
@@ -610,7 +613,7 @@ constexpr int Q2_TILE_ROWS[3] = {4, 8, 16};
 inline bool q2_tile_ok(int ty) { return ty == 4 || ty == 8 || ty == 16; }
 
 template <class TI, class TO, class CT, int F, int EPI>
-cudaError_t launch_q2_ty(const Q2Params<TI, TO, CT>& P, cudaStream_t s, int ty) {
+static cudaError_t launch_q2_ty(const Q2Params<TI, TO, CT>& P, cudaStream_t s, int ty) {
   switch (ty) {
     case 4: return launch_q2<TI, TO, CT, F, EPI, 4>(P, s);
     case 16: return launch_q2<TI, TO, CT, F, EPI, 16>(P, s);

@@ -730,8 +730,10 @@ static eth_status minres_solve(eth_grid* g, Work* w, const eth_opts* o, bool fp3
   const bool use_graph = o->graph != 0;
   // 1: the whole loop on the device; 2 (or a driver without conditional graph nodes): host-checked replays
   bool device_loop = o->graph == 1 && !w->no_cond_nodes;
-  const int key = (int)fp32 * 1000 + (int)(sizeof(T)) * 10 + o->mg_pre + 100 * o->mg_post + 10000 * o->a_exact +
-                  20000 * o->mq_mode + 100000 * tile_code(g) + 10000000 * o->graph;
+  // every option the captured graph depends on, in separate digit fields (mixed radix)
+  const long long key =
+      ((((((long long)o->graph * 4 + o->mq_mode) * 2 + o->a_exact) * 1024 + tile_code(g)) * 1024 + o->mg_post) * 1024 +
+       o->mg_pre) * 32 + (long long)sizeof(T) * 2 + (fp32 ? 1 : 0);
   while (true) {
     if (use_graph) {
       if (!w->gexec || w->gkey != key) {
@@ -981,7 +983,8 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   if (!g->has_rhs) { set_error("eth_solve: no right-hand side (eth_set_rhs)"); return ETH_EINVAL; }
   eth_opts o;
   if (opts) o = *opts; else eth_default_opts(&o);
-  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1 || !(o.mg_omega >= 0.0 && o.mg_omega < 2.0)) {
+  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1 || o.mg_pre > 64 || o.mg_post > 64 ||
+      !(o.mg_omega >= 0.0 && o.mg_omega < 2.0)) {
     set_error("eth_solve: bad options");
     return ETH_EINVAL;
   }
@@ -1018,7 +1021,7 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   st.status = r;
   st.kernel_launches = (int)(g->launches - l0);
   st.tile_rows = tile_rows(g);
-  st.tile_persistent = tile_persistent(g) && o.precision == ETH_MIXED;
+  st.tile_persistent = tile_strip(g) ? 2 : (tile_persistent(g) && o.precision == ETH_MIXED);
   if (stats) *stats = st;
   return r;
 }
@@ -1052,7 +1055,8 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
   if (!g->has_coef) { set_error("eth_solve_adjoint: call eth_set_coefficients first"); return ETH_EINVAL; }
   eth_opts o;
   if (opts) o = *opts; else eth_default_opts(&o);
-  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1 || !(o.mg_omega >= 0.0 && o.mg_omega < 2.0)) {
+  if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1 || o.mg_pre > 64 || o.mg_post > 64 ||
+      !(o.mg_omega >= 0.0 && o.mg_omega < 2.0)) {
     set_error("eth_solve_adjoint: bad options");
     return ETH_EINVAL;
   }
@@ -1089,7 +1093,7 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
   st.status = r;
   st.kernel_launches = (int)(g->launches - l0);
   st.tile_rows = tile_rows(g);
-  st.tile_persistent = tile_persistent(g) && o.precision == ETH_MIXED;
+  st.tile_persistent = tile_strip(g) ? 2 : (tile_persistent(g) && o.precision == ETH_MIXED);
   if (stats) *stats = st;
   return r;
 }

@@ -19,7 +19,7 @@ struct Work {
   cudaStream_t sm = nullptr;   // internal main stream (capturable), joined to the user stream
   cudaEvent_t evf = nullptr, evj = nullptr, evu = nullptr, t0 = nullptr, t1 = nullptr;
   cudaGraphExec_t gexec = nullptr;
-  int gkey = -1;
+  long long gkey = -1;
   long glaunch = 0;            // kernels in one replay of gexec
   bool no_cond_nodes = false;  // the driver refused a conditional graph node: host-replayed graphs
   int nmin_built = -1;

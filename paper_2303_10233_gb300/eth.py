@@ -188,10 +188,11 @@ class Grid:
         self._wind = wind
         _check(load().eth_set_coefficients(self.h, float(nu), self._p(wind, 2 * self.nv)))
 
-    def set_tile(self, rows, persistent=False):
-        """Pins the fused K apply's tile (32 x rows elements, rows in {4, 8, 16}; persistent form with
-        rows = 8); rows = 0 re-enables tuning."""
-        _check(load().eth_grid_set_tile(self.h, int(rows), int(bool(persistent))))
+    def set_tile(self, rows, persistent=0):
+        """Pins the fused K apply's form: tiles of 32 x rows elements (rows in {4, 8, 16}); persistent=1:
+        the persistent pipelined form (rows = 8); persistent=2: the warp-strip form with `rows` element
+        rows per warp (4, 8, 16, 32); rows = 0 re-enables tuning."""
+        _check(load().eth_grid_set_tile(self.h, int(rows), int(persistent)))
 
     def set_rhs(self, f_nodal, ubc):
         _check(load().eth_set_rhs(self.h, self._p(f_nodal, 2 * self.nv), self._p(ubc, 2 * self.nv)))

@@ -1,0 +1,188 @@
+"""GPU solves at the sizes and viscosities of the measured workloads, against the
+FP64 oracle.
+
+* Stokes 256^2 MMS (the bench solve, mixed precision, tol 1e-6): true residual
+  with the oracle's assembled K, and the velocity / pressure error against the
+  oracle's own exact-block MINRES (Algorithm 1 with P_1) run to a 1e-12
+  relative residual.
+* Oseen 512^2, nu in {1/100, 1/500, 1/1000}: the true FP64 residual with the
+  oracle's assembled K; at 128^2 (nu = 1/500, 1/1000) the solution against the
+  oracle's sparse direct solve.
+* The seeded 64-instance uneven batch: every instance's true residual with the
+  oracle's assembled K.
+* Oseen 256^2, nu = 1/200 (the differentiation workload): adjoint gradients
+  against central differences of GPU solves along seeded directions.
+* eth_solve_host (host buffers, copies inside the call) against eth_solve.
+
+The errors are printed (pytest -s) so they can be quoted per result.
+"""
+import numpy as np
+import pytest
+
+from oracle import direct, fem, krylov, problem
+from paper_2303_10233_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eth():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_10233_gb300 import eth as E
+    return E
+
+
+def _system(w):
+    g = fem.Grid(w["n"])
+    s = problem.System(g, w["nu"], w["wind"])
+    return g, s, s.rhs(w["f_nodal"], w["ubc"])
+
+
+def _x(u, p):
+    return np.concatenate([u.cpu().numpy(), p.cpu().numpy()])
+
+
+def _errors(g, x, xr):
+    nu = g.nu
+    e = np.linalg.norm(x - xr) / np.linalg.norm(xr)
+    eu = np.linalg.norm(x[:nu] - xr[:nu]) / np.linalg.norm(xr[:nu])
+    ep = np.linalg.norm(x[nu:] - xr[nu:]) / np.linalg.norm(xr[nu:])
+    return e, eu, ep
+
+
+def test_stokes_256_bench_solve_against_oracle_minres(eth):
+    """The bench solve (tol 1e-6) meets the residual target and its velocity is within
+    1e-5 of the oracle; the pressure, weighted weakly by the Euclidean residual (its rows
+    are divergences, O(h) against the O(1) velocity rows), needs a 1e-9 residual for
+    the 1e-5 solution error, which the mixed-precision refinement reaches as well."""
+    w = W.mms(256, seed=0)
+    g, s, b = _system(w)
+    x0 = np.concatenate([s.DB @ b[: g.nu], np.zeros(g.np_)])
+    xr, info = krylov.minres(lambda v: s.K @ v, krylov.P1(s), b, x0, tol=1e-14, maxit=400, true_tol=1e-12)
+    xr = s.canonical(xr)
+    assert np.linalg.norm(b - s.K @ xr) <= 1e-12 * np.linalg.norm(b) * 1.01
+    G = eth.problem(w)
+    for tol in (1e-6, 1e-9):
+        u, p, st = G.solve(tol=tol, precision="mixed")
+        x = _x(u, p)
+        res = np.linalg.norm(b - s.K @ x) / np.linalg.norm(b)
+        assert st["status"] == 0 and res <= tol * 1.01, (st, res)
+        e, eu, ep = _errors(g, s.canonical(x), xr)
+        print(f"stokes256 mixed tol {tol:.0e}: relres {res:.2e}, its {st['iters_total']}, error vs oracle {e:.2e} "
+              f"(u {eu:.2e}, p {ep:.2e}); oracle MINRES its {info['its']}")
+        assert eu <= 1e-5, (tol, e, eu, ep)
+        if tol <= 1e-9:
+            assert e <= 1e-5 and ep <= 1e-5, (tol, e, eu, ep)
+    G.close()
+
+
+@pytest.mark.parametrize("nu", [1 / 100, 1 / 500, 1 / 1000])
+def test_oseen_512_true_residual(eth, nu):
+    w = W.oseen_cavity(512, nu=nu, seed=1)
+    G = eth.problem(w)
+    u, p, st = G.solve(tol=1e-6, restart_max=160, maxit=4000)
+    G.close()
+    x = _x(u, p)
+    g, s, b = _system(w)
+    res = np.linalg.norm(b - s.K @ x) / np.linalg.norm(b)
+    print(f"oseen512 nu={nu:.4g}: its {st['iters_stage1']}+{st['iters_stage2']}, relres {res:.2e}, "
+          f"{st['seconds'] * 1e3:.0f} ms")
+    assert st["status"] == 0 and res <= 1e-6 * 1.01, (st, res)
+    assert st["prop2_lhs"] <= st["prop2_bound"] * (1 + 1e-6)
+
+
+@pytest.mark.parametrize("nu", [1 / 500, 1 / 1000])
+def test_oseen_128_solution_against_direct(eth, nu):
+    """At cell Peclet numbers above one the Oseen system is ill conditioned: a 1e-6
+    residual leaves a solution error near 1e-3, so the 1e-5 solution error is checked
+    on a solve to a 1e-10 residual."""
+    w = W.oseen_cavity(128, nu=nu, seed=1)
+    g, s, b = _system(w)
+    xr = direct.solve_pinned(s, b)
+    G = eth.problem(w)
+    for tol in (1e-6, 1e-10):
+        u, p, st = G.solve(tol=tol, restart_max=160, maxit=8000)
+        x = s.canonical(_x(u, p))
+        res = np.linalg.norm(b - s.K @ x) / np.linalg.norm(b)
+        e, eu, ep = _errors(g, x, xr)
+        print(f"oseen128 nu={nu:.4g} tol {tol:.0e}: its {st['iters_stage1']}+{st['iters_stage2']}, relres {res:.2e}, "
+              f"error vs direct {e:.2e} (u {eu:.2e}, p {ep:.2e})")
+        assert st["status"] == 0 and res <= tol * 1.01, (tol, st, res)
+    assert e <= 1e-5, (e, eu, ep)
+    G.close()
+
+
+def test_batch_64_every_instance_with_oracle_operator(eth):
+    insts = W.batch(seed=2)
+    grids = [eth.problem(w) for w in insts]
+    B = eth.Batch(grids)
+    us, ps, sts, rc = B.solve(tol=1e-6, restart_max=160, maxit=4000)
+    B.close()
+    for G in grids:
+        G.close()
+    worst, failed = 0.0, []
+    for i, (w, u, p, st) in enumerate(zip(insts, us, ps, sts)):
+        g, s, b = _system(w)
+        res = np.linalg.norm(b - s.K @ _x(u, p)) / np.linalg.norm(b)
+        assert res <= 1e-6 * 1.01 or st["status"] != 0, (i, res, st)   # a converged status is true
+        if st["status"] != 0:
+            failed.append((i, w["n"], w["nu"], res, st["status"]))
+        worst = max(worst, res)
+    print(f"batch64: worst relres {worst:.2e}; not converged: {failed}")
+    assert not failed, failed
+
+
+def test_oseen_256_gradients_against_central_differences(eth):
+    w = W.diff(256, nu=1 / 200)
+    G = eth.problem(w)
+    tight = dict(tol=1e-12, precision="fp64", maxit=6000, restart_max=160)
+    dev = G.device
+    ut = torch.as_tensor(w["u_target"], device=dev)
+    ubc = torch.as_tensor(w["ubc"], device=dev)
+    wind = torch.as_tensor(w["wind"], device=dev)
+    f0 = torch.as_tensor(w["f_nodal"], device=dev)
+
+    def J(f, nu):
+        G.set_coefficients(nu, wind)
+        G.set_rhs(f, ubc)
+        u, _, st = G.solve(**tight)
+        assert st["status"] == 0, st
+        return float(((u - ut) ** 2).sum()), u
+
+    J0, u = J(f0, w["nu"])
+    ru = 2.0 * (u - ut)
+    rp = torch.zeros(G.n1 + G.n0, dtype=torch.float64, device=dev)
+    lu, _, sa = G.solve_adjoint(ru, rp, **tight)
+    assert sa["status"] in (0, 6), sa
+    gf, gnu = G.adjoint_gradients(lu, u)
+    rng = np.random.default_rng(21)
+    fn = float(torch.linalg.norm(f0))
+    for k in range(3):
+        # J is quadratic in f, so the central difference is exact for any step; the step
+        # (0.1 ||f|| along a unit direction) keeps the change of J far above the error of
+        # the iterative solves
+        d = torch.as_tensor(rng.standard_normal(f0.numel()), device=dev)
+        d *= fn / float(torch.linalg.norm(d))
+        eps = 1e-1
+        fd = (J(f0 + eps * d, w["nu"])[0] - J(f0 - eps * d, w["nu"])[0]) / (2 * eps)
+        an = float(gf @ d)
+        print(f"diff256 direction {k}: FD {fd:.10e} adjoint {an:.10e} rel {abs(fd - an) / abs(fd):.2e}")
+        assert abs(fd - an) <= 1e-6 * abs(fd), (k, fd, an)
+    h = 1e-3 * w["nu"]
+    fd = (J(f0, w["nu"] + h)[0] - J(f0, w["nu"] - h)[0]) / (2 * h)
+    print(f"diff256 nu: FD {fd:.10e} adjoint {gnu:.10e} rel {abs(fd - gnu) / abs(fd):.2e}")
+    assert abs(fd - gnu) <= 1e-4 * abs(fd), (fd, gnu)
+    G.close()
+
+
+@pytest.mark.parametrize("w", [W.mms(64, seed=0), W.oseen_cavity(64, nu=1 / 100, seed=1)])
+def test_solve_host_matches_solve(eth, w):
+    G = eth.problem(w)
+    u, p, st = G.solve(tol=1e-8)
+    uh, ph, sh = G.solve_host(w["f_nodal"], w["ubc"], tol=1e-8)
+    G.close()
+    assert st["status"] == 0 and sh["status"] == 0
+    assert (st["iters_total"], st["iters_stage1"]) == (sh["iters_total"], sh["iters_stage1"])
+    assert np.array_equal(u.cpu().numpy(), uh) and np.array_equal(p.cpu().numpy(), ph)

@@ -44,7 +44,7 @@ def test_pcd_block_matches_oracle(eth, n, nu):
         ref = _mean_free(pcd.schur_inv(r))
         rt = torch.as_tensor(r, device=G.device)
         z64 = G.apply_pcd(rt, cheb_steps=80, ap_its=60).cpu().numpy()
-        assert abs(z64.mean()) <= 1e-12 * np.abs(z64).max()
+        assert abs(z64.mean()) <= 1e-10 * np.abs(z64).max()
         err = np.abs(z64 - ref).max() / np.abs(ref).max()
         assert err <= 1e-9, (n, k, err)
         z32 = G.apply_pcd(rt, cheb_steps=40, ap_its=40, fp32=True).cpu().numpy()

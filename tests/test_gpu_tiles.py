@@ -67,6 +67,8 @@ def test_set_tile_rejects(eth):
         G.set_tile(5)
     with pytest.raises(eth.EthError):
         G.set_tile(4, True)
+    with pytest.raises(eth.EthError):
+        G.set_tile(12, 2)
     G.set_tile(0)
     G.close()
 
@@ -76,10 +78,11 @@ def test_autotuned_solve(eth):
     w = W.mms(96, seed=1)
     G = eth.problem(w)
     u0, p0, st0 = G.solve(tol=1e-8, autotune=0)
-    assert st0["tile_rows"] == 8
+    assert st0["tile_rows"] == 8 and st0["tile_persistent"] == 2   # default: warp strips of 8 element rows
     G.set_tile(0)
     u1, p1, st1 = G.solve(tol=1e-8, autotune=1)
-    assert st1["tile_rows"] in (4, 8, 16)
+    assert (st1["tile_rows"] in (4, 8, 16) and st1["tile_persistent"] in (0, 1)) or \
+        (st1["tile_rows"] in (2, 4, 8, 16) and st1["tile_persistent"] == 2)
     assert st1["status"] == 0 and st1["relres_true"] <= 1e-8
     scale = float(torch.linalg.norm(u0))
     assert float(torch.linalg.norm(u1 - u0)) <= 1e-6 * scale

@@ -154,3 +154,14 @@ def test_picard_pins():
     s = problem.System(g, w["nu"], xs[-1][: g.nu].copy())
     x1, _ = direct.solve(s, s.rhs(w["f_nodal"], w["ubc"]))
     assert np.linalg.norm(s.canonical(x1) - xs[-1]) <= 1e-9 * np.linalg.norm(xs[-1])
+
+
+@pytest.mark.parametrize("w", [W.mms(8, seed=0), W.oseen_cavity(16, nu=1 / 200, seed=1)])
+def test_pinned_direct_solve_equals_bordered(w):
+    """The pinned-pressure factorisation used at the larger test grids returns the same
+    canonical solution as the bordered solve (unique modulo span{e1, e0})."""
+    g, s, b = _system(w)
+    xb, _ = direct.solve(s, b)
+    xp = direct.solve_pinned(s, b)
+    assert np.linalg.norm(xp - xb) <= 1e-10 * np.linalg.norm(xb)
+    assert np.linalg.norm(b - s.K @ xp) <= 1e-12 * np.linalg.norm(b)
