@@ -114,6 +114,15 @@ typedef struct {
                               restart_max (<= 160); 0 or <= restart: fixed  */
   double mg_omega;         /* damping of the velocity multigrid's Jacobi
                               smoother (0 < omega < 2); 0: 0.9               */
+  int oseen_prec;          /* Oseen grids: 0 the two-stage PCD method
+                              (Sec. 3.1); 1 one GMRES run on the full system
+                              with the LSC block-triangular preconditioner
+                              M_3 (Sec. 3.2, Eq. nse-precon-lsc), plain LSC
+                              (H = M)                                        */
+  int lsc_cg;              /* LSC: conjugate-gradient steps of each solve with
+                              the frame operator B M^{-1} B^T (block-diagonal
+                              Q1 / cell-centred P0 V-cycle preconditioner);
+                              0: 6                                           */
 } eth_opts;
 
 typedef struct {

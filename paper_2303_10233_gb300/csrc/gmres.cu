@@ -793,7 +793,7 @@ static eth_status precond_m1(eth_grid* g, Work* w, const eth_opts* o, const doub
   return vel_part<T>(g, w, o, r, z + nu2, true, z, done, adj);
 }
 
-// y = K x for the active system (stage 1: reduced [F B1^T; B1 0], stage 2: full)
+// y = K x for the active system (stage 1: reduced [F B1^T; B1 0], stages 2 and 3: full)
 static eth_status sys_apply(eth_grid* g, int stage, bool fp32, bool trans, const double* x, double* y) {
   const eth_op op = stage == 1 ? (trans ? ETH_OP_K1T : ETH_OP_K1) : (trans ? ETH_OP_KT : ETH_OP_K);
   return op_apply(g, op, fp32, x, y);
@@ -815,6 +815,7 @@ static eth_status gm_iter_kernels(eth_grid* g, Work* w, const eth_opts* o, int s
   k_gm_col_in<<<nb, 256, 0, g->s>>>(ntv, G->V, ld, G->gs, G->vin);
   ETH_CUDA(cudaGetLastError());
   if (stage == 1) ETH_TRY(precond_pcd<T>(g, w, o, G->vin, G->zout, done, adj));
+  else if (stage == 3) ETH_TRY(precond_lsc<T>(g, w, o, G->vin, G->zout, done, adj));
   else ETH_TRY(precond_m1<T>(g, w, o, G->vin, G->zout, done, adj));
   k_gm_col_out<<<nb, 256, 0, g->s>>>(ntv, G->zout, G->Z, ld, G->gs);
   ETH_CUDA(cudaGetLastError());
@@ -919,6 +920,7 @@ static eth_status gmres_run(eth_grid* g, Work* w, const eth_opts* o, int stage, 
       double* Vj = G->V + (size_t)j * ld;
       double* Zj = G->Z + (size_t)j * ld;
       if (stage == 1) ETH_TRY(precond_pcd<T>(g, w, o, Vj, Zj, done, adj));
+      else if (stage == 3) ETH_TRY(precond_lsc<T>(g, w, o, Vj, Zj, done, adj));
       else ETH_TRY(precond_m1<T>(g, w, o, Vj, Zj, done, adj));
       ETH_TRY(sys_apply(g, stage, fp32, adj, Zj, G->w));
       double* h1 = &G->gs->h1[0];
@@ -1013,6 +1015,37 @@ static eth_status two_stage(eth_grid* g, Work* w, const eth_opts* o, eth_stats* 
   return st->relres_true <= eta * (1.0 + 1e-9) ? ETH_OK : ETH_ENOTCONV;
 }
 
+// One flexible GMRES run on the full system with the LSC preconditioner M_3 (Sec. 3.2)
+// from the lifted boundary data to eta ||b||; the stage statistics report it as Step II.
+template <class T>
+static eth_status lsc_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adj, const double* b) {
+  const size_t nt = g->nt;
+  GMRESWork* G = w->gm;
+  ETH_TRY(lsc_prepare<T>(g, w));   // allocations before the Arnoldi step is captured
+  k_oseen_scalars<<<1, 1, 0, g->s>>>(g->sc, (double)g->n1, (double)g->n0, 16.0 / (g->hx * g->hy), -g->nu);
+  k_prop2<<<gb(nt), 256, 0, g->s>>>(nt, nt, b, G->part, G->ticket + 5, &G->gs->pcg[0]);
+  ETH_CUDA(cudaGetLastError());
+  ETH_CUDA(cudaMemcpyAsync(G->gsh, G->gs, sizeof(GScalars), cudaMemcpyDeviceToHost, g->s));
+  ETH_CUDA(cudaStreamSynchronize(g->s));
+  const double nb2 = std::sqrt(G->gsh->pcg[0]);
+  if (!std::isfinite(nb2)) { st->relres_true = nb2; return ETH_ENAN; }
+  if (!(nb2 > 0.0)) { ETH_CUDA(cudaMemsetAsync(w->x, 0, nt * 8, g->s)); st->relres_true = 0; return ETH_OK; }
+  int its = 0, s2 = 0, e2 = 0;
+  double res = 0;
+  ETH_TRY(gmres_run<T>(g, w, o, 3, adj, b, w->x, nt, o->tol * nb2, o->maxit, &its, &res, &s2, &e2));
+  ETH_TRY(canonicalize(g, w->x));
+  double rr;
+  ETH_TRY(true_residual(g, w, b, &rr, adj));
+  st->iters_stage1 = 0;
+  st->iters_stage2 = its;
+  st->iters_total = its;
+  st->refine_passes = 0;
+  st->escalations = e2;
+  st->relres_true = std::sqrt(rr) / nb2;
+  if (s2 == ETH_ENAN || !std::isfinite(st->relres_true)) return ETH_ENAN;
+  return st->relres_true <= o->tol * (1.0 + 1e-9) ? ETH_OK : ETH_ENOTCONV;
+}
+
 // M_S^{-1} rp alone, with chosen inner step counts (eth_apply_pcd).
 template <class T>
 static eth_status apply_pcd_t(eth_grid* g, Work* w, bool adjoint, int cheb, int its, const double* rp, double* zp) {
@@ -1037,10 +1070,10 @@ eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, b
   eth_status r;
   if (o->precision == ETH_MIXED) {
     ETH_TRY(ensure_hier<float>(g, w, o));
-    r = two_stage<float>(g, w, o, st, adjoint, w->bp);
+    r = o->oseen_prec == 1 ? lsc_solve<float>(g, w, o, st, adjoint, w->bp) : two_stage<float>(g, w, o, st, adjoint, w->bp);
   } else {
     ETH_TRY(ensure_hier<double>(g, w, o));
-    r = two_stage<double>(g, w, o, st, adjoint, w->bp);
+    r = o->oseen_prec == 1 ? lsc_solve<double>(g, w, o, st, adjoint, w->bp) : two_stage<double>(g, w, o, st, adjoint, w->bp);
   }
   // the solve used the projected right-hand side; report a removed component as for Stokes
   if (r == ETH_OK && std::isfinite(nbp) && nbp > 0.0 && incons > 1e-8 * nbp) r = ETH_EINCONSISTENT;

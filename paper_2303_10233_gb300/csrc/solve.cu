@@ -18,6 +18,7 @@ static void work_free(void* p) {
   Work* w = (Work*)p;
   if (!w) return;
   gmres_free(w);
+  lsc_free(w);
   mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd); mg_free(w->vft); mg_free(w->vdt);
   cudaFree(w->x); cudaFree(w->d); cudaFree(w->r); cudaFree(w->Kz); cudaFree(w->bp); cudaFree(w->pcg);
   for (int k = 0; k < 2; ++k) { cudaFree(w->V[k]); cudaFree(w->Z[k]); cudaFree(w->W[k]); }
@@ -990,6 +991,10 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   }
   if ((o.a_exact || o.mq_mode == ETH_MQ_EXACT) && !(o.inner_tol > 0)) { set_error("eth_solve: bad inner_tol"); return ETH_EINVAL; }
   if (o.precision != ETH_FP64 && o.precision != ETH_MIXED) { set_error("eth_solve: bad precision"); return ETH_EINVAL; }
+  if (o.oseen_prec < 0 || o.oseen_prec > 1 || o.lsc_cg < 0 || o.lsc_cg > 100) {
+    set_error("eth_solve: oseen_prec must be 0 or 1 and lsc_cg in 0..100");
+    return ETH_EINVAL;
+  }
   ETH_ON_DEVICE(g);
   eth_stats st;
   std::memset(&st, 0, sizeof(st));
@@ -1056,7 +1061,8 @@ eth_status eth_solve_adjoint(eth_grid* g, const eth_opts* opts, const double* ru
   eth_opts o;
   if (opts) o = *opts; else eth_default_opts(&o);
   if (!(o.tol > 0) || o.maxit < 1 || o.mg_pre < 1 || o.mg_post < 1 || o.mg_pre > 64 || o.mg_post > 64 ||
-      !(o.mg_omega >= 0.0 && o.mg_omega < 2.0)) {
+      !(o.mg_omega >= 0.0 && o.mg_omega < 2.0) || o.oseen_prec < 0 || o.oseen_prec > 1 || o.lsc_cg < 0 ||
+      o.lsc_cg > 100) {
     set_error("eth_solve_adjoint: bad options");
     return ETH_EINVAL;
   }

@@ -25,6 +25,7 @@ struct Work {
   int nmin_built = -1;
   GMRESWork* gm = nullptr;     // GMRES / PCD workspace (Oseen)
   double* pcg = nullptr;       // exact-block inner PCG vectors (4 x 2 N_v + 6 x N_1)
+  void* lscw[2] = {nullptr, nullptr};   // LSC preconditioner workspaces (FP32, FP64; lsc.cu)
 };
 
 
@@ -63,6 +64,12 @@ template <class T>
 Hier<T>& vel_hier_t(Work* w);
 eth_status adjoint_gradients(eth_grid* g, Work* w, const double* lu, const double* u, double* grad_f, double* grad_nu);
 void gmres_free(Work* w);
+void lsc_free(Work* w);
+// z = M_3^{-1} r, the LSC block-triangular preconditioner (Sec. 3.2) of the full Oseen system
+template <class T>
+eth_status lsc_prepare(eth_grid* g, Work* w);
+template <class T>
+eth_status precond_lsc(eth_grid* g, Work* w, const eth_opts* o, const double* r, double* z, const int* done, bool adj);
 eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* b);
 
 // Runs the solver body on the handle's internal stream (capturable even when

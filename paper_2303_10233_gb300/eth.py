@@ -38,7 +38,8 @@ class Opts(ctypes.Structure):
                 ("mg_post", ctypes.c_int), ("mg_min_n", ctypes.c_int), ("mq_mode", ctypes.c_int),
                 ("a_exact", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("refine_inner_tol", ctypes.c_double), ("graph", ctypes.c_int), ("verbose", ctypes.c_int),
-                ("autotune", ctypes.c_int), ("restart_max", ctypes.c_int), ("mg_omega", ctypes.c_double)]
+                ("autotune", ctypes.c_int), ("restart_max", ctypes.c_int), ("mg_omega", ctypes.c_double),
+                ("oseen_prec", ctypes.c_int), ("lsc_cg", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -127,6 +128,8 @@ def make_opts(**kw):
             raise KeyError(f"unknown option {k}")
         if k == "precision" and isinstance(v, str):
             v = {"fp64": 0, "mixed": 1}[v]
+        if k == "oseen_prec" and isinstance(v, str):
+            v = {"pcd": 0, "lsc": 1}[v]
         setattr(o, k, v)
     return o
 
