@@ -76,8 +76,11 @@ typedef enum {
 /* Precision of the internal arithmetic. */
 typedef enum { ETH_FP64 = 0, ETH_MIXED = 1 } eth_precision;
 
-/* Approximation of the singular pressure mass solve M_Q^+ (Sec. 2.2-2.3). */
-typedef enum { ETH_MQ_VCYCLE = 0, ETH_MQ_EXACT = 1 } eth_mq_mode;
+/* Approximation of the singular pressure mass solve M_Q^+ (Sec. 2.2-2.3):
+ * VCYCLE the block elimination of Q0 with one Q1 V-cycle (default); EXACT inner
+ * PCG to inner_tol (the P_1 form of Sec. 2.4); CHEB the Chebyshev semi-iteration
+ * on multicolour symmetric Gauss-Seidel (the M_cheb block of P_2, Sec. 2.3-2.4). */
+typedef enum { ETH_MQ_VCYCLE = 0, ETH_MQ_EXACT = 1, ETH_MQ_CHEB = 2 } eth_mq_mode;
 
 typedef struct {
   double tol;              /* relative true residual ||b-Kx||/||b||          */
@@ -123,6 +126,10 @@ typedef struct {
                               the frame operator B M^{-1} B^T (block-diagonal
                               Q1 / cell-centred P0 V-cycle preconditioner);
                               0: 6                                           */
+  int mq_cheb_steps;       /* ETH_MQ_CHEB: Chebyshev steps; 0: 20 (Sec. 2.4)  */
+  double mq_cheb_a;        /* ETH_MQ_CHEB: lower end a of the Chebyshev
+                              interval [a, 1] (smallest nonzero eigenvalue of
+                              the SGS-preconditioned M_Q); 0: 0.655 / n^2     */
 } eth_opts;
 
 typedef struct {
@@ -266,6 +273,16 @@ eth_status eth_apply_k_dot_static(int n, double x0, double x1, double y0, double
  * g's stream. */
 eth_status eth_apply_pcd(eth_grid* g, int adjoint, int fp32, int cheb_steps, int ap_its, const double* rp_dev,
                          double* zp_dev);
+
+/* The cheap pressure-mass approximation of P_2 alone (Sec. 2.3-2.4): z = steps
+ * steps of the Chebyshev semi-iteration on the interval [a, b] (a <= 0: 0.655 / n^2;
+ * b <= 0: 1) preconditioned by symmetric Gauss-Seidel on M_Q in five colours (the
+ * four parity classes of the Q1 nodes, then the P0 elements; forward, then back),
+ * for M_Q z = r with r's component along k = [1; -1] removed first; z is returned
+ * orthogonal to k (Euclidean).  r_dev, z_dev: device, N_1 + N_0 FP64 each
+ * ([Q1; P0] layout, caller-owned).  fp32 != 0 runs the iteration in FP32.
+ * ETH_EINVAL for steps outside 1..10000 or a >= b.  Asynchronous on g's stream. */
+eth_status eth_apply_mqcheb(eth_grid* g, int fp32, int steps, double a, double b, const double* r_dev, double* z_dev);
 
 /* Picard iteration for the steady Navier-Stokes problem (Sec. 3: the Oseen
  * systems are its linearisations).  g must be an ETH_OSEEN grid whose viscosity

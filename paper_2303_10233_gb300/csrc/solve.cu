@@ -19,6 +19,7 @@ static void work_free(void* p) {
   if (!w) return;
   gmres_free(w);
   lsc_free(w);
+  mqcheb_free(w);
   mg_free(w->vf); mg_free(w->qf); mg_free(w->vd); mg_free(w->qd); mg_free(w->vft); mg_free(w->vdt);
   cudaFree(w->x); cudaFree(w->d); cudaFree(w->r); cudaFree(w->Kz); cudaFree(w->bp); cudaFree(w->pcg);
   for (int k = 0; k < 2; ++k) { cudaFree(w->V[k]); cudaFree(w->Z[k]); cudaFree(w->W[k]); }
@@ -623,6 +624,7 @@ static eth_status precond_stokes(eth_grid* g, Work* w, const eth_opts* o, const 
   ETH_CUDA(cudaEventRecord(w->evf, g->s));
   ETH_CUDA(cudaStreamWaitEvent(w->s2, w->evf, 0));
   if (o->mq_mode == ETH_MQ_EXACT) ETH_TRY(precond_pressure_exact<T>(g, w, o, v + nu2, z + nu2, gs, nbv, done, w->s2));
+  else if (o->mq_mode == ETH_MQ_CHEB) ETH_TRY(precond_pressure_cheb<T>(g, w, o, v + nu2, z + nu2, gs, nbv, done, w->s2));
   else ETH_TRY(precond_pressure<T>(g, q1_hier<T>(w), v + nu2, z + nu2, gs, nbv, done, w->s2));
   if (o->a_exact) {
     ETH_TRY(vel_pcg<T>(g, w, o, v, z, 60));
@@ -990,6 +992,10 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
     return ETH_EINVAL;
   }
   if ((o.a_exact || o.mq_mode == ETH_MQ_EXACT) && !(o.inner_tol > 0)) { set_error("eth_solve: bad inner_tol"); return ETH_EINVAL; }
+  if (o.mq_mode < 0 || o.mq_mode > 2 || o.mq_cheb_steps < 0 || o.mq_cheb_steps > 1000 || !(o.mq_cheb_a >= 0.0 && o.mq_cheb_a < 1.0)) {
+    set_error("eth_solve: bad mq_mode / mq_cheb_steps / mq_cheb_a");
+    return ETH_EINVAL;
+  }
   if (o.precision != ETH_FP64 && o.precision != ETH_MIXED) { set_error("eth_solve: bad precision"); return ETH_EINVAL; }
   if (o.oseen_prec < 0 || o.oseen_prec > 1 || o.lsc_cg < 0 || o.lsc_cg > 100) {
     set_error("eth_solve: oseen_prec must be 0 or 1 and lsc_cg in 0..100");
@@ -1003,6 +1009,8 @@ eth_status eth_solve(eth_grid* g, const eth_opts* opts, double* u, double* p, et
   StreamSwap guard(g, w);
   if (o.precision == ETH_MIXED) ETH_TRY(ensure_hier<float>(g, w, &o)); else ETH_TRY(ensure_hier<double>(g, w, &o));
   if (o.a_exact || o.mq_mode == ETH_MQ_EXACT) ETH_TRY(ensure_pcg(g, w));
+  if (o.mq_mode == ETH_MQ_CHEB)   // workspace before the solver graph is captured
+    ETH_TRY(o.precision == ETH_MIXED ? mqcheb_prepare<float>(g, w) : mqcheb_prepare<double>(g, w));
   if (o.autotune) ETH_TRY(tune_tiles(g, o.precision == ETH_MIXED));
   const long l0 = g->launches;
   ETH_CUDA(cudaEventRecord(w->t0, g->s));

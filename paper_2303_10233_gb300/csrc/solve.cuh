@@ -26,6 +26,7 @@ struct Work {
   GMRESWork* gm = nullptr;     // GMRES / PCD workspace (Oseen)
   double* pcg = nullptr;       // exact-block inner PCG vectors (4 x 2 N_v + 6 x N_1)
   void* lscw[2] = {nullptr, nullptr};   // LSC preconditioner workspaces (FP32, FP64; lsc.cu)
+  void* mcw[2] = {nullptr, nullptr};    // Chebyshev-SGS M_Q workspaces (FP32, FP64; mqcheb.cu)
 };
 
 
@@ -65,6 +66,14 @@ Hier<T>& vel_hier_t(Work* w);
 eth_status adjoint_gradients(eth_grid* g, Work* w, const double* lu, const double* u, double* grad_f, double* grad_nu);
 void gmres_free(Work* w);
 void lsc_free(Work* w);
+void mqcheb_free(Work* w);
+double mqcheb_default_a(const eth_grid* g);
+template <class T>
+eth_status mqcheb_prepare(eth_grid* g, Work* w);
+// MINRES pressure block nu M_cheb^{-1} (the cheap M_Q of P_2, Sec. 2.3-2.4), mqcheb.cu
+template <class T>
+eth_status precond_pressure_cheb(eth_grid* g, Work* w, const eth_opts* o, const double* vp, double* zp, const Slot& gsl,
+                                 int goff, const int* done, cudaStream_t s);
 // z = M_3^{-1} r, the LSC block-triangular preconditioner (Sec. 3.2) of the full Oseen system
 template <class T>
 eth_status lsc_prepare(eth_grid* g, Work* w);

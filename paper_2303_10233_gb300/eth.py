@@ -39,7 +39,8 @@ class Opts(ctypes.Structure):
                 ("a_exact", ctypes.c_int), ("inner_tol", ctypes.c_double),
                 ("refine_inner_tol", ctypes.c_double), ("graph", ctypes.c_int), ("verbose", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("restart_max", ctypes.c_int), ("mg_omega", ctypes.c_double),
-                ("oseen_prec", ctypes.c_int), ("lsc_cg", ctypes.c_int)]
+                ("oseen_prec", ctypes.c_int), ("lsc_cg", ctypes.c_int), ("mq_cheb_steps", ctypes.c_int),
+                ("mq_cheb_a", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -90,6 +91,7 @@ def load(path=LIB_PATH):
         "eth_adjoint_gradients": (i, [vp, vp, vp, vp, ctypes.POINTER(d)]),
         "eth_apply_k_dot_static": (i, [i, d, d, d, d, d, i, vp, vp, vp, vp]),
         "eth_apply_pcd": (i, [vp, i, i, i, i, vp, vp]),
+        "eth_apply_mqcheb": (i, [vp, i, i, d, d, vp, vp]),
         "eth_batch_create": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "eth_batch_solve": (i, [vp, ctypes.POINTER(Opts), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)]),
         "eth_batch_destroy": (None, [vp]),
@@ -130,6 +132,8 @@ def make_opts(**kw):
             v = {"fp64": 0, "mixed": 1}[v]
         if k == "oseen_prec" and isinstance(v, str):
             v = {"pcd": 0, "lsc": 1}[v]
+        if k == "mq_mode" and isinstance(v, str):
+            v = {"vcycle": 0, "exact": 1, "cheb": 2}[v]
         setattr(o, k, v)
     return o
 
@@ -223,6 +227,14 @@ class Grid:
         _check(load().eth_apply_pcd(self.h, int(bool(adjoint)), int(bool(fp32)), int(cheb_steps), int(ap_its),
                                     self._p(rp, self.n1), self._p(zp, self.n1)))
         return zp
+
+    def apply_mqcheb(self, r, steps=20, a=0.0, b=0.0, fp32=False):
+        """Chebyshev-SGS approximation of M_Q^+ r (the M_cheb block of P_2), k projected out."""
+        m = self.n1 + self.n0
+        z = self._zeros(m)
+        _check(load().eth_apply_mqcheb(self.h, int(bool(fp32)), int(steps), float(a), float(b), self._p(r, m),
+                                       self._p(z, m)))
+        return z
 
     def solve(self, u=None, p=None, **opts):
         u = self._zeros(2 * self.nv) if u is None else u
