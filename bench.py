@@ -16,7 +16,8 @@ outside the per-step CUDA-event timing.
 ``--impl reference`` times the FP64 CPU oracle (SciPy, exact-block MINRES)
 on a bounded number of iterations of the same workload.  The default run also
 reports the oracle's whole solve to tolerance (cpu_baseline), the Oseen 512^2
-two-stage solve (oseen512) and the roofline of the K apply (roofline).
+two-stage solve (oseen512), the uneven 64-instance batch (batch64) and the
+roofline of the K apply (roofline).
 """
 from __future__ import annotations
 
@@ -313,6 +314,8 @@ def run_ours(args):
 
     # ---- Oseen 512^2 (two-stage PCD GMRES, nu = 1/100): time to tolerance, mixed and FP64
     oseen = oseen_line(torch, eth, W, local)
+    # ---- the uneven 64-instance batch, concurrent mixed vs plain FP64 one at a time
+    batch = batch_line(torch, eth, W, local) if not args.no_batch else None
 
     # ---- roofline of the dominant kernel, timed live on the launching stream
     roof = roofline(G, torch, eth)
@@ -345,6 +348,7 @@ def run_ours(args):
         "gpu_launches": launches,
         "roofline": roof,
         "oseen512": oseen,
+        "batch64": batch,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "wall_s": t_wall,
@@ -409,6 +413,40 @@ def oseen_line(torch, eth, W, dev, steps=3):
                      "mdof_iter_s": O.nt * its / (t / 1e3) / 1e6}
     out["speedup_mixed_vs_fp64"] = out["fp64"]["ms"] / out["mixed"]["ms"]
     O.close()
+    return out
+
+
+def batch_line(torch, eth, W, dev):
+    """The seeded uneven batch (64 Stokes / Oseen instances, n in {32, 64, 128, 256},
+    nu log-uniform in [1e-3, 1e-1]): wall time of one concurrent mixed-precision batch
+    solve to 1e-6 (Oseen instances with the LSC preconditioner M_3), after a warm-up
+    solve that also runs the autotuners, against the plain FP64 form solved one
+    instance at a time; N_t x iterations summed over the instances / wall time."""
+    insts = W.batch(seed=2)
+    grids = [eth.problem(w, device=dev) for w in insts]
+    opts = dict(tol=TOL, oseen_prec="lsc", restart=150, maxit=4000)
+    B = eth.Batch(grids)
+    B.solve(**opts)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    _, _, sts, rc = B.solve(**opts)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    B.close()
+    work = sum(G.nt * st["iters_total"] for G, st in zip(grids, sts))
+    t = time.perf_counter()
+    its64 = 0
+    for G in grids:
+        _, _, st = G.solve(precision="fp64", graph=0, **opts)
+        its64 += st["iters_total"]
+    torch.cuda.synchronize()
+    wall64 = time.perf_counter() - t
+    out = {"workload": "batch64_seed2", "sum_N_t": sum(G.nt for G in grids), "wall_s": wall, "status": rc,
+           "converged": sum(1 for st in sts if st["status"] == 0), "iters": sum(st["iters_total"] for st in sts),
+           "mdof_iter_s": work / wall / 1e6, "fp64_one_at_a_time_s": wall64,
+           "speedup_mixed_batched_vs_fp64": wall64 / wall}
+    for G in grids:
+        G.close()
     return out
 
 
@@ -553,6 +591,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-instance batch measurement")
     ap.add_argument("--profile-apply", type=int, default=0, metavar="N",
                     help="only run the fused K apply (FP32 math) 5 times on an N x N grid (for ncu captures)")
     ap.add_argument("--profile-kind", default="stokes", choices=["stokes", "oseen"])

@@ -1058,10 +1058,18 @@ static eth_status apply_pcd_t(eth_grid* g, Work* w, bool adjoint, int cheb, int 
   return pcd_schur<T>(g, w, rp, zp, 1.0, cheb, its, nullptr);
 }
 
-eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* bsrc) {
+// GMRES workspace and the Gram-Schmidt autotuning of an Oseen grid ahead of its solve
+// (the batch driver runs this for every instance before the instances overlap, so the
+// tuner times its kernels on an otherwise idle GPU)
+eth_status oseen_prepare(eth_grid* g, Work* w, const eth_opts* o) {
   const int m = std::max(1, std::min(std::max(o->restart, o->restart_max), GM_MAX));
   ETH_TRY(gm_alloc(g, w, m));
   if (o->autotune && !w->gm->grp_tuned) ETH_TRY(tune_cgs(g, w->gm));
+  return ETH_OK;
+}
+
+eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* bsrc) {
+  ETH_TRY(oseen_prepare(g, w, o));
   // consistent right-hand side (e1 / e0 components removed)
   ETH_CUDA(cudaMemcpyAsync(w->bp, bsrc, (size_t)g->nt * 8, cudaMemcpyDeviceToDevice, g->s));
   ETH_TRY(canonicalize(g, w->bp));

@@ -1156,6 +1156,11 @@ eth_status eth_batch_solve(eth_batch* b, const eth_opts* opts, double* const* u,
       eth_grid* g = b->grids[i];
       ETH_ON_DEVICE(g);
       ETH_TRY(tune_tiles(g, o.precision == ETH_MIXED));
+      if (g->kind == ETH_OSEEN) {   // the Gram-Schmidt tuner as well (GMRES workspace first)
+        Work* w;
+        ETH_TRY(work_get(g, &w));
+        ETH_TRY(oseen_prepare(g, w, &o));
+      }
     }
   auto worker = [&]() {   // eth_solve makes each instance's device current
     while (true) {

@@ -80,6 +80,7 @@ eth_status lsc_prepare(eth_grid* g, Work* w);
 template <class T>
 eth_status precond_lsc(eth_grid* g, Work* w, const eth_opts* o, const double* r, double* z, const int* done, bool adj);
 eth_status oseen_solve(eth_grid* g, Work* w, const eth_opts* o, eth_stats* st, bool adjoint, const double* b);
+eth_status oseen_prepare(eth_grid* g, Work* w, const eth_opts* o);
 
 // Runs the solver body on the handle's internal stream (capturable even when
 // the user stream is the legacy default stream), ordered after and before the
