@@ -469,7 +469,7 @@ def _time_apply(torch, eth, H, fp32, reps=40):
     return e0.elapsed_time(e1) / reps / 1e3
 
 
-ROOF_ROWS = (2, 4, 8)   # warp-strip shapes timed; the fastest is the roofline kernel
+ROOF_ROWS = (4, 6, 8)   # warp-strip shapes timed; the fastest is the roofline kernel
 
 
 def roofline(G, torch, eth):

@@ -105,7 +105,7 @@ typedef struct {
                               fused K apply with tiles of 32 x {4, 8, 16}
                               elements per CTA, the persistent 32 x 8 form
                               (mixed precision) and the warp-strip form with
-                              {2, 4, 8, 16} element rows per warp, and keep
+                              {2, 4, 6, 8, 16} element rows per warp, and keep
                               the fastest (cached
                               per grid size, operator and precision for the
                               process), and for GMRES the basis vectors per
@@ -170,8 +170,8 @@ void eth_grid_destroy(eth_grid* g);
  * resident CTAs that walk over the tiles and copy the next tile's input
  * (cp.async) while computing the current one (FP32 element arithmetic only;
  * FP64 applies use 32 x 8 one tile per CTA); or, with persistent = 2, the
- * warp-strip form (the default): each warp walks `rows` element rows (2, 4, 8,
- * 16 or 32) of a strip of 30 element columns, keeping the shared node row in
+ * warp-strip form (the default): each warp walks `rows` element rows (2 to 32)
+ * of a strip of 30 element columns, keeping the shared node row in
  * registers (FP32 or FP64 element arithmetic).  Turns the autotuner off for this
  * grid; rows = 0 restores the default and lets the next solve with
  * opts.autotune tune again.  Every apply gives bitwise the same K x whatever

@@ -173,7 +173,7 @@ eth_status tune_tiles(eth_grid* g, bool fp32) {
   int best = TILE_STRIP + 8;
   float best_ms = 1e30f;
   eth_status st = ETH_OK;
-  const int cands[8] = {4, 8, 16, 8 + TILE_PERSIST, 2 + TILE_STRIP, 4 + TILE_STRIP, 8 + TILE_STRIP, 16 + TILE_STRIP};
+  const int cands[9] = {4, 8, 16, 8 + TILE_PERSIST, 2 + TILE_STRIP, 4 + TILE_STRIP, 6 + TILE_STRIP, 8 + TILE_STRIP, 16 + TILE_STRIP};
   for (int ty : cands) {
     if (ty >= TILE_PERSIST && ty < TILE_STRIP && !fp32) continue;
     if (ty < TILE_PERSIST && q2_blocks(g->n, ty) > g->part_cap) continue;
@@ -209,7 +209,7 @@ extern "C" eth_status eth_grid_set_tile(eth_grid* g, int rows, int persistent) {
   ETH_ON_DEVICE(g);
   if (rows == 0) { g->tile_rows = 0; g->tuned = false; return ETH_OK; }
   if (persistent == 2) {   // warp-strip kernel, `rows` element rows per warp
-    if (!q2s_rows_ok(rows)) { set_error("eth_grid_set_tile: strip rows=%d not in {2, 4, 8, 16, 32}", rows); return ETH_EINVAL; }
+    if (!q2s_rows_ok(rows)) { set_error("eth_grid_set_tile: strip rows=%d not in 2..32", rows); return ETH_EINVAL; }
     if (q2s_blocks(g->n, rows) > g->part_cap) { set_error("eth_grid_set_tile: too many strips for n=%d", g->n); return ETH_EINVAL; }
     g->tile_rows = rows + TILE_STRIP;
     g->tuned = true;

@@ -29,6 +29,20 @@ namespace eth {
 constexpr int QS_OWN = 30;     // owned element columns per warp (lanes 1 .. 30)
 constexpr int QS_WARPS = 4;    // warps per CTA
 constexpr int TILE_STRIP = 200;   // tile codes TILE_STRIP + rows select this kernel
+#ifndef ETH_STRIP_MINB
+#define ETH_STRIP_MINB 5       // resident CTAs per SM the FP32 Stokes form is compiled for
+#endif
+#ifndef ETH_STRIP_STCS
+#define ETH_STRIP_STCS 1       // 1: outputs stored with the streaming (evict-first) hint
+#endif
+// output store: the outputs are not read again by the kernel
+__device__ __forceinline__ void strip_st(double* p, double v) {
+#if ETH_STRIP_STCS
+  __stcs(p, v);
+#else
+  *p = v;
+#endif
+}
 
 // ---------------------------------------------------------------------------
 // Element arithmetic in the even/odd basis, one velocity component at a time.
@@ -468,7 +482,7 @@ __device__ __forceinline__ void strip_warp(const Q2Params<double, double, CT>& P
               else dacc += o * xc[g];
             }
           }
-          yc[g] = o;
+          strip_st(yc + g, o);
         };
         emit(i0, j0, rowB || colB, Y[0] + L2 + carV[c], uB[c][0]);
         if (xin) emit(i1, j0, rowB, Y[1] + carE[c], uB[c][1]);
@@ -494,7 +508,7 @@ __device__ __forceinline__ void strip_warp(const Q2Params<double, double, CT>& P
         const int gp = ey * M + ex;
         const CT sp = YP1[0] + LP1 + carP;
         const double so = cvt_out<double, CT>(sp);
-        P.yp[gp] = so;
+        strip_st(P.yp + gp, so);
         if (DOT) {
           if constexpr (sizeof(CT) == 4) fdot += sp * pB[0];
           else dacc += so * P.dvp[gp];
@@ -502,7 +516,7 @@ __device__ __forceinline__ void strip_warp(const Q2Params<double, double, CT>& P
         if (HP0 && xin && yin) {
           const int ge = n1 + ey * n + ex;
           const double s0 = cvt_out<double, CT>(Z0);
-          P.yp[ge] = s0;
+          strip_st(P.yp + ge, s0);
           if (DOT) {
             if constexpr (sizeof(CT) == 4) fdot += Z0 * p0v;
             else dacc += s0 * P.dvp[ge];
@@ -526,7 +540,7 @@ __device__ __forceinline__ void strip_warp(const Q2Params<double, double, CT>& P
 }
 
 template <class CT, int F>
-__global__ void __launch_bounds__(32 * QS_WARPS, (sizeof(CT) == 4 && !(F & QF_CONV)) ? 5 : 1)
+__global__ void __launch_bounds__(32 * QS_WARPS, (sizeof(CT) == 4 && !(F & QF_CONV)) ? ETH_STRIP_MINB : 1)
     k_q2s(Q2Params<double, double, CT> P, int rows, int nstrips, int nwork) {
   ETH_GRID_DEP_WAIT();
   constexpr bool DOT = F & QF_DOT;
@@ -556,7 +570,7 @@ __global__ void __launch_bounds__(32 * QS_WARPS, (sizeof(CT) == 4 && !(F & QF_CO
 
 inline int q2s_warps(int n, int rows) { return (int)(cdiv(n + 1, QS_OWN) * cdiv(n + 1, rows)); }
 inline int q2s_blocks(int n, int rows) { return (int)cdiv(q2s_warps(n, rows), QS_WARPS); }
-inline bool q2s_rows_ok(int rows) { return rows == 2 || rows == 4 || rows == 8 || rows == 16 || rows == 32; }
+inline bool q2s_rows_ok(int rows) { return rows >= 2 && rows <= 32; }
 
 template <class CT, int F>
 static cudaError_t launch_q2s(const Q2Params<double, double, CT>& P, cudaStream_t s, int rows) {

@@ -68,7 +68,7 @@ def test_set_tile_rejects(eth):
     with pytest.raises(eth.EthError):
         G.set_tile(4, True)
     with pytest.raises(eth.EthError):
-        G.set_tile(12, 2)
+        G.set_tile(40, 2)
     G.set_tile(0)
     G.close()
 
