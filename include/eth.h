@@ -47,6 +47,7 @@ extern "C" {
 
 typedef struct eth_grid eth_grid;
 typedef struct eth_batch eth_batch;
+typedef struct eth_mgrid eth_mgrid;
 
 typedef enum {
   ETH_OK = 0,
@@ -323,6 +324,80 @@ eth_status eth_lanczos(eth_grid* g, int cap, double* delta_dev, double* gamma_de
  * Asynchronous on g's stream; g only supplies the stream.  One warp per j:
  * each multisection round evaluates 32 Sturm counts of O(j) work. */
 eth_status eth_est_infsup(eth_grid* g, const double* delta_dev, const double* gamma_dev, int k, double* est_dev);
+
+/* ------------------------------------------------------------------------
+ * Masked grids: inflow-outflow domains (Sec. 3, Test problem 3, the flow over
+ * a step).  The domain is the union of the ACTIVE squares of an nx x ny grid of
+ * square elements of side h on the box [x0, x0 + nx h] x [y0, y0 + ny h];
+ * active_host[ey*nx + ex] != 0 marks element (ex, ey) active.  Unknowns live on
+ * the full lattice of the box with the square-grid layout above (N_v =
+ * (2nx+1)(2ny+1), N_1 = (nx+1)(ny+1), N_0 = nx ny); those of inactive nodes and
+ * elements keep identity rows of K.  Node roles: a Q2 node is active when it
+ * belongs to an active element, interior when every element around it is
+ * active; the Dirichlet nodes are the active non-interior nodes except, with
+ * outflow = 1, those strictly inside the right edge of the box (x = x0 + nx h),
+ * where the weak form leaves the natural (do-nothing) outflow condition.
+ * Velocity rows and columns of the Dirichlet and inactive nodes are treated as
+ * on the square grid.  With an outflow boundary the pressure null space is
+ * span{[0; k]}, k = 1 on the active Q1 nodes and -1 on the active elements.
+ * Ownership, streams and errors as for eth_grid; all vectors FP64 device.
+ * ------------------------------------------------------------------------ */
+
+/* Creates a masked-grid handle (nx, ny >= 1, h > 0, outflow in {0, 1}, at
+ * least one active element) on the current device; active_host holds nx*ny
+ * bytes.  Builds the multigrid hierarchy of the velocity blocks: nx and ny are
+ * halved while both are even and every 2 x 2 block of elements is wholly
+ * active or inactive, and the coarsest level is solved exactly, so it may keep
+ * at most 2048 free velocity nodes (ETH_EINVAL otherwise). */
+eth_status eth_mgrid_create(int nx, int ny, double h, double x0, double y0, const unsigned char* active_host,
+                            int outflow, void* cuda_stream, eth_mgrid** out);
+void eth_mgrid_destroy(eth_mgrid* g);
+/* N_v, N_1, N_0 and N_t = 2 N_v + N_1 + N_0 (any pointer may be NULL). */
+eth_status eth_mgrid_sizes(const eth_mgrid* g, long long* nv, long long* n1, long long* n0, long long* nt);
+/* Host copies of the node roles (N_v bytes: 1 on fixed = Dirichlet or inactive
+ * velocity nodes; N_v bytes: 1 on Dirichlet nodes; N_1 bytes: 1 on active Q1
+ * nodes), the number of multigrid levels and the free nodes of the coarsest
+ * level; any pointer may be NULL. */
+eth_status eth_mgrid_roles(const eth_mgrid* g, unsigned char* fixed_host, unsigned char* dirichlet_host,
+                           unsigned char* q1_active_host, int* levels, int* coarse_free);
+/* Viscosity nu > 0 and the nodal Q2 wind (device, 2 N_v; NULL: the Stokes
+ * operator F = nu A). */
+eth_status eth_mgrid_set_coefficients(eth_mgrid* g, double nu, const double* wind_dev);
+/* y = op(x) on the masked grid: ETH_OP_K (N_t), ETH_OP_K1 (reduced system on
+ * [u; p1], 2 N_v + N_1), ETH_OP_A, ETH_OP_F (2 N_v, Dirichlet and inactive rows
+ * identity), ETH_OP_B (2 N_v -> N_1 + N_0, B D_I u over the active elements,
+ * zero rows for inactive unknowns), ETH_OP_BT (N_1 + N_0 -> 2 N_v, D_I B^T p),
+ * ETH_OP_MQ (the pressure mass over the active elements, zero rows for inactive
+ * unknowns).  FP64 element arithmetic; other operators give ETH_EINVAL.
+ * Asynchronous on the handle's stream. */
+eth_status eth_mgrid_apply(eth_mgrid* g, eth_op op, const double* x_dev, double* y_dev);
+/* Lifted right-hand side from the Dirichlet data u_b (device, 2 N_v; entries
+ * off the Dirichlet nodes are ignored, no body force):
+ * b = [D_I (-F u_b) + D_B u_b; -B u_b]. */
+eth_status eth_mgrid_rhs(eth_mgrid* g, const double* ubc_dev, double* b_dev);
+/* Solves K x = b (outflow = 1 only) by the two-stage PCD method of Sec. 3.1
+ * from the lifted initial guess x0 = [D_B b_u; 0] (x's content on entry is
+ * ignored): Step I restarted flexible GMRES(opts->restart) on the reduced
+ * system with [F B1^T; 0 -M_S]^{-1}, M_S^{-1} = Ap^{-1} F1 Q1^{-1} (F1 = nu K1 +
+ * N1(w) plus the inflow Robin term -int_{Gamma_in} (w.n) p q ds, Ap = B1 Md^{-1}
+ * B1^T), to ||r|| <= c_stage tol ||b_red||; Step II GMRES on K with M_1 =
+ * [F B^T; 0 -(1/nu) M_Q]^{-1} to tol ||b||.  F^{-1} is one V-cycle of the
+ * masked multigrid (FP32 levels, damped Jacobi, streamline diffusion on the
+ * levels of an Oseen operator), Ap^{-1} and M_Q^+ inner Jacobi PCG, Q1^{-1} ten
+ * Chebyshev steps.  On exit k^T p = 0.  stats: stage iterations, the FP64 true
+ * relative residual, the Prop. 2 quantities (||z*||^2 and its bound), status
+ * ETH_ENOTCONV when tol was not reached within opts->maxit.  Synchronises. */
+eth_status eth_mgrid_solve(eth_mgrid* g, const eth_opts* opts, const double* b_dev, double* x_dev, eth_stats* stats);
+/* Picard iteration (Sec. 3, Test problem 3: the Oseen system after steps-1
+ * fixed-point steps from the Stokes solution): step 1 solves the Stokes
+ * problem, step k+1 the Oseen problem with the wind w = u_k, each by
+ * eth_mgrid_solve with the right-hand side of u_b.  x_dev (N_t): the last
+ * iterate; xs_dev (steps x N_t, may be NULL): every iterate; nlres_host (steps,
+ * may be NULL): ||b(u_k) - K(u_k) x_k|| / ||b(u_k)||; stats_host (steps, may be
+ * NULL).  The viscosity comes from eth_mgrid_set_coefficients; on return the
+ * coefficients are those linearised at the last iterate. */
+eth_status eth_mgrid_picard(eth_mgrid* g, const eth_opts* opts, const double* ubc_dev, int steps, double* x_dev,
+                            double* xs_dev, double* nlres_host, eth_stats* stats_host);
 
 /* Batched solves of independent instances (each created with its own handle,
  * all on the same stream). */

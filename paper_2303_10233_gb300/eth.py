@@ -92,6 +92,16 @@ def load(path=LIB_PATH):
         "eth_apply_k_dot_static": (i, [i, d, d, d, d, d, i, vp, vp, vp, vp]),
         "eth_apply_pcd": (i, [vp, i, i, i, i, vp, vp]),
         "eth_apply_mqcheb": (i, [vp, i, i, d, d, vp, vp]),
+        "eth_mgrid_create": (i, [i, i, d, d, d, vp, i, vp, ctypes.POINTER(vp)]),
+        "eth_mgrid_destroy": (None, [vp]),
+        "eth_mgrid_sizes": (i, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong)]),
+        "eth_mgrid_roles": (i, [vp, vp, vp, vp, pi, pi]),
+        "eth_mgrid_set_coefficients": (i, [vp, d, vp]),
+        "eth_mgrid_apply": (i, [vp, i, vp, vp]),
+        "eth_mgrid_rhs": (i, [vp, vp, vp]),
+        "eth_mgrid_solve": (i, [vp, ctypes.POINTER(Opts), vp, vp, ctypes.POINTER(Stats)]),
+        "eth_mgrid_picard": (i, [vp, ctypes.POINTER(Opts), vp, i, vp, vp, ctypes.POINTER(d), ctypes.POINTER(Stats)]),
         "eth_batch_create": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp)]),
         "eth_batch_solve": (i, [vp, ctypes.POINTER(Opts), ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(Stats)]),
         "eth_batch_destroy": (None, [vp]),
@@ -379,6 +389,103 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class MGrid:
+    """Handle of a masked uniform grid (wraps eth_mgrid): the active squares of an
+    nx x ny box of square elements of side h from (x0, y0); ``outflow`` makes the
+    box's right edge a natural outflow boundary (Sec. 3, Test problem 3)."""
+
+    def __init__(self, nx, ny, h, x0, y0, active, outflow=True, stream=None, device=None):
+        import torch
+        L = load()
+        act = np.ascontiguousarray(np.asarray(active, dtype=bool).reshape(int(ny), int(nx)).astype(np.uint8))
+        self.nx, self.ny, self.h = int(nx), int(ny), float(h)
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if self.stream.device != self.device:
+            raise ValueError(f"stream of {self.stream.device} for a grid on {self.device}")
+        hnd = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(L.eth_mgrid_create(self.nx, self.ny, self.h, float(x0), float(y0),
+                                      act.ctypes.data_as(ctypes.c_void_p), int(bool(outflow)),
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(hnd)))
+        self.h_ = hnd
+        q = [ctypes.c_longlong() for _ in range(4)]
+        _check(L.eth_mgrid_sizes(self.h_, *[ctypes.byref(v) for v in q]))
+        self.nv, self.n1, self.n0, self.nt = (v.value for v in q)
+
+    def close(self):
+        if getattr(self, "h_", None):
+            load().eth_mgrid_destroy(self.h_)
+            self.h_ = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _p(self, t, numel):
+        return _ptr(t, numel, self.device)
+
+    def _zeros(self, m):
+        import torch
+        return torch.zeros(m, dtype=torch.float64, device=self.device)
+
+    def roles(self):
+        """Host arrays (fixed velocity nodes, Dirichlet nodes, active Q1 nodes), the number of
+        multigrid levels and the free nodes of the coarsest level."""
+        fx = np.zeros(self.nv, dtype=np.uint8); dr = np.zeros(self.nv, dtype=np.uint8)
+        qa = np.zeros(self.n1, dtype=np.uint8)
+        lv, cf = ctypes.c_int(), ctypes.c_int()
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _check(load().eth_mgrid_roles(self.h_, c(fx), c(dr), c(qa), ctypes.byref(lv), ctypes.byref(cf)))
+        return fx.astype(bool), dr.astype(bool), qa.astype(bool), lv.value, cf.value
+
+    def set_coefficients(self, nu, wind=None):
+        self._wind = wind
+        _check(load().eth_mgrid_set_coefficients(self.h_, float(nu), self._p(wind, 2 * self.nv)))
+
+    def _op_sizes(self, op):
+        u2, pp, u1 = 2 * self.nv, self.n1 + self.n0, 2 * self.nv + self.n1
+        return {"K": (self.nt, self.nt), "K1": (u1, u1), "A": (u2, u2), "F": (u2, u2), "B": (u2, pp),
+                "BT": (pp, u2), "MQ": (pp, pp)}[op]
+
+    def apply(self, op, x):
+        nin, nout = self._op_sizes(op)
+        y = self._zeros(nout)
+        _check(load().eth_mgrid_apply(self.h_, OPS[op], self._p(x, nin), self._p(y, nout)))
+        return y
+
+    def rhs(self, ubc):
+        b = self._zeros(self.nt)
+        _check(load().eth_mgrid_rhs(self.h_, self._p(ubc, 2 * self.nv), self._p(b, self.nt)))
+        return b
+
+    def solve(self, b, **opts):
+        x = self._zeros(self.nt)
+        o = make_opts(**opts)
+        st = Stats()
+        rc = load().eth_mgrid_solve(self.h_, ctypes.byref(o), self._p(b, self.nt), self._p(x, self.nt), ctypes.byref(st))
+        if rc not in SOFT:
+            _check(rc)
+        return x, st.as_dict()
+
+    def picard(self, ubc, steps, keep_all=False, **opts):
+        """Picard iteration from the Stokes solution; returns (last iterate, every iterate or None,
+        nonlinear residual per step, stats per step)."""
+        import torch
+        x = self._zeros(self.nt)
+        xs = torch.zeros(steps * self.nt, dtype=torch.float64, device=self.device) if keep_all else None
+        o = make_opts(**opts)
+        res = (ctypes.c_double * steps)()
+        st = (Stats * steps)()
+        rc = load().eth_mgrid_picard(self.h_, ctypes.byref(o), self._p(ubc, 2 * self.nv), int(steps),
+                                     self._p(x, self.nt), self._p(xs, steps * self.nt), res, st)
+        if rc not in SOFT:
+            _check(rc)
+        return x, (xs.view(steps, self.nt) if keep_all else None), list(res), [s_.as_dict() for s_ in st]
 
 
 def torch_float64():

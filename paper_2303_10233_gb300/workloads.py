@@ -23,6 +23,11 @@ Workloads (all on [-1, 1]^2):
 * ``diff``        -- the differentiation problem (Oseen 256^2, nu = 1/200).
 * ``tridiagonal`` -- random symmetric tridiagonal coefficients (diagonal and
                      positive off-diagonal), the shape of a Lanczos record.
+* ``step``        -- the flow over a step (Sec. 3, Test problem 3): the element
+                     mask of D = [-1, 0) x [0, 1] U [0, 5] x [-1, 1] on the box
+                     [-1, 5] x [-1, 1] with square elements of side 1/m, and the
+                     parabolic inflow u = (4y(1 - y), 0) at x = -1.
+* ``channel``     -- the channel [0, L] x [-1, 1] with the inflow (1 - y^2, 0).
 """
 from __future__ import annotations
 
@@ -199,3 +204,45 @@ def tridiagonal(k, seed=0):
     sits below a k x k block)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-1.0, 2.0, k), rng.uniform(0.05, 1.0, k)
+
+
+def _box_lattice(nx, ny, h, x0, y0):
+    xs = x0 + 0.5 * h * np.arange(2 * nx + 1)
+    ys = y0 + 0.5 * h * np.arange(2 * ny + 1)
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    return X.ravel(), Y.ravel()
+
+
+def _inflow(nx, ny, h, x0, y0, active, profile):
+    """u = (profile(y), 0) on the nodes of the box's left edge that touch an active
+    element (the inflow boundary), zero elsewhere."""
+    X, Y = _box_lattice(nx, ny, h, x0, y0)
+    N = 2 * nx + 1
+    ub = np.zeros(2 * X.size)
+    act = np.asarray(active, dtype=bool).reshape(ny, nx)
+    for j in range(2 * ny + 1):
+        eys = [j // 2] if j % 2 else [j // 2 - 1, j // 2]
+        if any(0 <= ey < ny and act[ey, 0] for ey in eys):
+            ub[j * N] = profile(Y[j * N])
+    return ub
+
+
+def step(m, nu=1.0 / 50.0):
+    """The step problem with h = 1/m: nx = 6m, ny = 2m elements on [-1, 5] x [-1, 1]."""
+    nx, ny, h = 6 * m, 2 * m, 1.0 / m
+    xc = -1.0 + h * (np.arange(nx) + 0.5)
+    yc = -1.0 + h * (np.arange(ny) + 0.5)
+    XC, YC = np.meshgrid(xc, yc, indexing="xy")
+    active = ~((XC < 0.0) & (YC < 0.0))
+    ubc = _inflow(nx, ny, h, -1.0, -1.0, active, lambda y: 4.0 * y * (1.0 - y))
+    return {"nx": nx, "ny": ny, "h": h, "x0": -1.0, "y0": -1.0, "active": active, "nu": float(nu), "ubc": ubc,
+            "outflow": True}
+
+
+def channel(m, length=2.0, nu=0.02):
+    """[0, length] x [-1, 1] with h = 1/m, inflow u = (1 - y^2, 0) at x = 0, outflow at x = length."""
+    nx, ny, h = int(round(length * m)), 2 * m, 1.0 / m
+    active = np.ones((ny, nx), dtype=bool)
+    ubc = _inflow(nx, ny, h, 0.0, -1.0, active, lambda y: 1.0 - y ** 2)
+    return {"nx": nx, "ny": ny, "h": h, "x0": 0.0, "y0": -1.0, "active": active, "nu": float(nu), "ubc": ubc,
+            "outflow": True}
