@@ -491,9 +491,10 @@ __global__ void k_f1_elem(int nx, int ny, double h, double nu, const unsigned ch
 
 // Q1 node operator with identity rows on the inactive nodes:
 // y_I = sum over active elements T around I of (M_T x)_I, M_T = F1e[T]
-// (F1e != nullptr) or the Q1 mass h^2 m (x) m.
+// (F1e != nullptr) or h^2 (m (x) m + c1) (c1 = 0: the Q1 mass; c1 = -1/16: the
+// Schur complement S = Qk - R^T Q0^{-1} R of M_Q, element by element).
 __global__ void k_q1apply(int nx, int ny, double h, const unsigned char* __restrict__ act, const unsigned char* __restrict__ q1a,
-                          const double* __restrict__ F1e, const double* __restrict__ x, double* __restrict__ y) {
+                          const double* __restrict__ F1e, double c1, const double* __restrict__ x, double* __restrict__ y) {
   const int M = nx + 1;
   const size_t n1 = (size_t)M * (ny + 1);
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1; k += (size_t)gridDim.x * blockDim.x) {
@@ -509,7 +510,7 @@ __global__ void k_q1apply(int nx, int ny, double h, const unsigned char* __restr
         const int c = 1 - dx, d = 1 - dy, li = d * 2 + c;
         for (int lj = 0; lj < 4; ++lj) {
           const int cj = lj & 1, dj = lj >> 1;
-          const double m = F1e != nullptr ? F1e[e * 16 + li * 4 + lj] : h * h * q1m(c, cj) * q1m(d, dj);
+          const double m = F1e != nullptr ? F1e[e * 16 + li * 4 + lj] : h * h * (q1m(c, cj) * q1m(d, dj) + c1);
           s += m * x[(size_t)(ey + dj) * M + ex + cj];
         }
       }
@@ -555,13 +556,13 @@ __global__ void k_mq_apply(int nx, int ny, double h, const unsigned char* __rest
 }
 
 // Diagonal data of the PCD and M_Q solves:
-//  mdinv (N_v): inverse diagonal of the velocity mass matrix on the free nodes, 0 on fixed ones;
+//  mdinv (N_v): inverse diagonal of the velocity mass matrix on the free nodes, 0 on fixed ones
+//  (the Md of Ap = B1 Md^{-1} B1^T);
 //  q1dinv (N_1): inverse diagonal of the Q1 mass (1 on inactive nodes);
-//  mqdinv (N_1 + N_0): inverse diagonal of M_Q (1 on inactive unknowns);
 //  kv (N_1 + N_0): the frame vector k (1 on active Q1 nodes, -1 on active elements).
 __global__ void k_diag_setup(int nx, int ny, double h, const unsigned char* __restrict__ act, const unsigned char* __restrict__ fix,
                              const unsigned char* __restrict__ q1a, double* __restrict__ mdinv, double* __restrict__ q1dinv,
-                             double* __restrict__ mqdinv, double* __restrict__ kv) {
+                             double* __restrict__ kv) {
   const int Nx = 2 * nx + 1, M = nx + 1;
   const size_t nv = (size_t)Nx * (2 * ny + 1), n1 = (size_t)M * (ny + 1), n0 = (size_t)nx * ny;
   const double area = h * h;
@@ -595,50 +596,11 @@ __global__ void k_diag_setup(int nx, int ny, double h, const unsigned char* __re
       }
       const double d = cnt * area / 9.0;
       q1dinv[q] = q1a[q] ? 1.0 / d : 1.0;
-      mqdinv[q] = q1dinv[q];
       kv[q] = q1a[q] ? 1.0 : 0.0;
     } else {
       const size_t e = k - nv - n1;
-      mqdinv[n1 + e] = act[e] ? 1.0 / area : 1.0;
       kv[n1 + e] = act[e] ? -1.0 : 0.0;
     }
-  }
-}
-
-// Inverse diagonal of Ap = B1 Md^{-1} B1^T (free velocity columns) on the
-// active Q1 nodes, 1 on the inactive ones: diag_I = sum_j (B1x_Ij^2 + B1y_Ij^2) / Md_j
-// over the 5 x 5 patch of Q2 nodes around I, B1's entries summed from the
-// element matrices -h c12 (x) g12 and -h g12 (x) c12.
-__global__ void k_ap_diag(int nx, int ny, double h, const unsigned char* __restrict__ act, const unsigned char* __restrict__ q1a,
-                          const double* __restrict__ mdinv, double* __restrict__ apdinv) {
-  const int Nx = 2 * nx + 1, Ny = 2 * ny + 1, M = nx + 1;
-  const size_t n1 = (size_t)M * (ny + 1);
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1; k += (size_t)gridDim.x * blockDim.x) {
-    if (!q1a[k]) { apdinv[k] = 1.0; continue; }
-    const int J = (int)(k / M), I = (int)(k - (size_t)J * M);
-    double bx[5][5], by[5][5];
-    for (int a = 0; a < 5; ++a)
-      for (int b = 0; b < 5; ++b) { bx[a][b] = 0; by[a][b] = 0; }
-    for (int dy = 0; dy < 2; ++dy)
-      for (int dx = 0; dx < 2; ++dx) {
-        const int ex = I - 1 + dx, ey = J - 1 + dy;
-        if (ex < 0 || ex >= nx || ey < 0 || ey >= ny || !act[(size_t)ey * nx + ex]) continue;
-        const int cc = 1 - dx, dd = 1 - dy;
-        for (int b = 0; b < 3; ++b)
-          for (int a = 0; a < 3; ++a) {
-            const int pa = 2 * dx + a, pb = 2 * dy + b;   // 2 (ex - I + 1) + a, likewise in y
-            bx[pb][pa] += -h * c12(cc, a) * g12(dd, b);
-            by[pb][pa] += -h * g12(cc, a) * c12(dd, b);
-          }
-      }
-    double s = 0;
-    for (int pb = 0; pb < 5; ++pb)
-      for (int pa = 0; pa < 5; ++pa) {
-        const int gi = 2 * I - 2 + pa, gj = 2 * J - 2 + pb;
-        if (gi < 0 || gi >= Nx || gj < 0 || gj >= Ny) continue;
-        s += (bx[pb][pa] * bx[pb][pa] + by[pb][pa] * by[pb][pa]) * mdinv[(size_t)gj * Nx + gi];
-      }
-    apdinv[k] = s > 0.0 ? 1.0 / s : 1.0;
   }
 }
 
@@ -684,25 +646,6 @@ struct PcgS {
   int done, its, pad;
 };
 
-// r = b (k-projected when kv != nullptr, s = <k, b>), x = 0, z = D^{-1} r, p = z
-__global__ void __launch_bounds__(RB) k_pcg_init(size_t m, const double* __restrict__ b, const double* __restrict__ kv,
-                                                 const double* __restrict__ s, double kk, const double* __restrict__ dinv,
-                                                 double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
-                                                 double* __restrict__ x, PcgS* st, double tol2, Slot sl) {
-  const double f = kv != nullptr ? s[0] / kk : 0.0;
-  double v[2] = {0.0, 0.0};
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
-    const double rv = kv != nullptr ? b[k] - f * kv[k] : b[k];
-    const double zv = dinv[k] * rv;
-    r[k] = rv; z[k] = zv; p[k] = zv; x[k] = 0.0;
-    v[0] += rv * zv;
-    v[1] += rv * rv;
-  }
-  if (slot_arrive<2>(sl, blockIdx.x, v)) {
-    st->rz = v[0]; st->rr0 = v[1]; st->tol2 = tol2; st->its = 0; st->alpha = 0; st->beta = 0;
-    st->done = (v[1] == 0.0 || v[0] <= 0.0) ? 1 : 0;
-  }
-}
 // alpha = rz / <p, q>
 __global__ void __launch_bounds__(RB) k_pcg_alpha(size_t m, const double* __restrict__ p, const double* __restrict__ q, PcgS* st, Slot sl) {
   if (st->done) return;
@@ -711,28 +654,6 @@ __global__ void __launch_bounds__(RB) k_pcg_alpha(size_t m, const double* __rest
   if (slot_arrive<1>(sl, blockIdx.x, v)) {
     if (v[0] > 0.0) st->alpha = st->rz / v[0];
     else st->done = 1;
-  }
-}
-// x += alpha p, r -= alpha q, z = D^{-1} r; beta = <r, z>_new / <r, z>; convergence test on ||r||^2
-__global__ void __launch_bounds__(RB) k_pcg_xr(size_t m, const double* __restrict__ p, const double* __restrict__ q,
-                                               const double* __restrict__ dinv, double* __restrict__ x, double* __restrict__ r,
-                                               double* __restrict__ z, PcgS* st, Slot sl) {
-  if (st->done) return;
-  const double al = st->alpha;
-  double v[2] = {0.0, 0.0};
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
-    x[k] += al * p[k];
-    const double rv = r[k] - al * q[k];
-    const double zv = dinv[k] * rv;
-    r[k] = rv; z[k] = zv;
-    v[0] += rv * zv;
-    v[1] += rv * rv;
-  }
-  if (slot_arrive<2>(sl, blockIdx.x, v)) {
-    st->beta = v[0] / st->rz;
-    st->rz = v[0];
-    st->its += 1;
-    if (v[1] <= st->tol2 * st->rr0 || !(v[0] > 0.0)) st->done = 1;
   }
 }
 // p = z + beta p
@@ -808,8 +729,26 @@ struct MLev {
   double h = 0;
   size_t nv = 0, n0 = 0;
   unsigned char *act = nullptr, *fix = nullptr;   // device masks
+  std::vector<unsigned char> hact;                // host element mask
   bool own = false;                               // masks owned (coarse levels)
   float *dinv = nullptr, *w = nullptr, *x = nullptr, *b = nullptr, *r = nullptr, *t = nullptr;
+};
+
+// one level of a masked Q1 hierarchy (FP64)
+struct QLev {
+  int nx = 0, ny = 0;
+  size_t n1 = 0;
+  const unsigned char* act = nullptr;    // the velocity level's element mask
+  unsigned char* q1a = nullptr;          // active Q1 nodes (device)
+  std::vector<unsigned char> hq1a;
+  double *d = nullptr, *x = nullptr, *b = nullptr, *r = nullptr;
+};
+struct QHier {
+  std::vector<QLev> lv;
+  double shift = 0.0;
+  double* cinv = nullptr;
+  int* cidx = nullptr;
+  int ncf = 0;
 };
 
 // Node roles of a masked grid (the definitions of the header comment).
@@ -886,6 +825,8 @@ static bool invert_dense(std::vector<double>& A, int m) {
 }  // namespace eth
 
 using eth::msk::MLev;
+using eth::msk::QHier;
+using eth::msk::QLev;
 using eth::msk::PcgS;
 
 struct eth_mgrid {
@@ -904,13 +845,13 @@ struct eth_mgrid {
   unsigned* ticket = nullptr;
   double* red = nullptr;        // reduction results (device, 64)
   double* redh = nullptr;       // pinned mirror (64)
-  double *mdinv = nullptr, *q1dinv = nullptr, *mqdinv = nullptr, *apdinv = nullptr, *kv = nullptr, *f1e = nullptr;
+  double *mdinv = nullptr, *q1dinv = nullptr, *kv = nullptr, *f1e = nullptr;
   double kk = 0.0;
   double *t0 = nullptr, *t1 = nullptr, *t2 = nullptr, *xs = nullptr;          // N_t scratch
   double *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *px = nullptr, *pa = nullptr, *pb = nullptr;  // N_1 + N_0
-  PcgS* pcg = nullptr;
-  PcgS* pcgh = nullptr;
+  PcgS* pcg = nullptr;           // inner CG scalars (device)
   std::vector<MLev> lv;
+  eth::msk::QHier qh[2];        // Q1 hierarchies: [0] Ap preconditioner, [1] Schur complement of M_Q
   float* E32 = nullptr;         // level element outputs (18 N_0 of level 0)
   float* cinv = nullptr;
   int* cidx = nullptr;
@@ -919,7 +860,6 @@ struct eth_mgrid {
   int gm_m = 0;                 // restart length the GMRES workspace holds
   double* bv = nullptr;         // right-hand side buffer of the Picard iteration (N_t)
   long launches = 0;
-  int pcg_its = 0;              // inner PCG steps of the last solve
 };
 
 namespace eth {
@@ -1016,6 +956,12 @@ static void mg_free(G* g) {
     cudaFree(L.dinv); cudaFree(L.w); cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); cudaFree(L.t);
   }
   g->lv.clear();
+  for (QHier& Q : g->qh) {
+    for (QLev& L : Q.lv) { cudaFree(L.q1a); cudaFree(L.d); cudaFree(L.x); cudaFree(L.b); cudaFree(L.r); }
+    Q.lv.clear();
+    cudaFree(Q.cinv); cudaFree(Q.cidx);
+    Q.cinv = nullptr; Q.cidx = nullptr; Q.ncf = 0;
+  }
   cudaFree(g->E32); g->E32 = nullptr;
   cudaFree(g->cinv); g->cinv = nullptr;
   cudaFree(g->cidx); g->cidx = nullptr;
@@ -1031,6 +977,7 @@ static eth_status mg_build_geometry(G* g) {
   for (int l = 0;; ++l) {
     MLev L;
     L.nx = nx; L.ny = ny; L.h = h;
+    L.hact = act;
     L.nv = (size_t)(2 * nx + 1) * (2 * ny + 1);
     L.n0 = (size_t)nx * ny;
     if (l == 0) {
@@ -1243,17 +1190,294 @@ static eth_status vcycle(G* g, const double* v, double* z, int pre, int post, fl
 }  // namespace eth
 
 // ---------------------------------------------------------------------------
+// masked Q1 multigrid: the preconditioner of the PCD matrix Ap (Q1 Laplacian
+// plus a unit shift on the outflow nodes, where Ap = B1 Md^{-1} B1^T does not
+// annihilate the constants) and of the Schur complement S = Qk - R^T Q0^{-1} R
+// of M_Q (pure Q1 Laplacian with natural boundary conditions, singular on the
+// constants, pseudo-inverse on the coarsest level)
+// ---------------------------------------------------------------------------
+namespace eth {
+namespace msk {
+
+constexpr double Q1_SHIFT = 1.0;   // outflow shift of the Ap preconditioner's operator
+constexpr double Q1_OMEGA = 0.8;   // damped Jacobi of the Q1 levels
+
+// K1 node operator over the active elements (+ shift on the outflow nodes when
+// shift > 0): mode 0 y = K1 x (identity rows on inactive nodes), mode 1
+// y = b - K1 x, mode 2 y = x + omega d (b - K1 x) (0 on inactive nodes)
+__global__ void k_k1node(int nx, int ny, int mode, double shift, const unsigned char* __restrict__ act,
+                         const unsigned char* __restrict__ q1a, const double* __restrict__ x, const double* __restrict__ b,
+                         const double* __restrict__ d, double omega, double* __restrict__ y) {
+  const int M = nx + 1;
+  const size_t n1 = (size_t)M * (ny + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1; k += (size_t)gridDim.x * blockDim.x) {
+    if (!q1a[k]) { y[k] = mode == 0 ? x[k] : 0.0; continue; }
+    const int J = (int)(k / M), I = (int)(k - (size_t)J * M);
+    double s = (shift > 0.0 && I == nx) ? shift * x[k] : 0.0;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const int ex = I - 1 + dx, ey = J - 1 + dy;
+        if (ex < 0 || ex >= nx || ey < 0 || ey >= ny || !act[(size_t)ey * nx + ex]) continue;
+        const int c = 1 - dx, dd = 1 - dy;
+        for (int lj = 0; lj < 4; ++lj) {
+          const int cj = lj & 1, dj = lj >> 1;
+          s += (q1k(c, cj) * q1m(dd, dj) + q1m(c, cj) * q1k(dd, dj)) * x[(size_t)(ey + dj) * M + ex + cj];
+        }
+      }
+    y[k] = mode == 0 ? s : (mode == 1 ? b[k] - s : x[k] + omega * d[k] * (b[k] - s));
+  }
+}
+// inverse diagonal of the level operator: 2/3 per active element around the node (+ shift), 0 on inactive nodes
+__global__ void k_k1dinv(int nx, int ny, double shift, const unsigned char* __restrict__ act, const unsigned char* __restrict__ q1a,
+                         double* __restrict__ d) {
+  const int M = nx + 1;
+  const size_t n1 = (size_t)M * (ny + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1; k += (size_t)gridDim.x * blockDim.x) {
+    if (!q1a[k]) { d[k] = 0.0; continue; }
+    const int J = (int)(k / M), I = (int)(k - (size_t)J * M);
+    double s = (shift > 0.0 && I == nx) ? shift : 0.0;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const int ex = I - 1 + dx, ey = J - 1 + dy;
+        if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && act[(size_t)ey * nx + ex]) s += 2.0 / 3.0;
+      }
+    d[k] = 1.0 / s;
+  }
+}
+// b_c = P^T r_f (bilinear interpolation transposed), 0 on inactive coarse nodes
+__global__ void k_q1r(int nxc, int nyc, const unsigned char* __restrict__ q1ac, const double* __restrict__ rf, double* __restrict__ bc) {
+  const int Mc = nxc + 1, Mf = 2 * nxc + 1, Nyf = 2 * nyc + 1;
+  const size_t n1c = (size_t)Mc * (nyc + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1c; k += (size_t)gridDim.x * blockDim.x) {
+    if (!q1ac[k]) { bc[k] = 0.0; continue; }
+    const int J = (int)(k / Mc), I = (int)(k - (size_t)J * Mc);
+    double s = 0.0;
+    for (int u = -1; u <= 1; ++u) {
+      const int fj = 2 * J + u;
+      if (fj < 0 || fj >= Nyf) continue;
+      for (int v = -1; v <= 1; ++v) {
+        const int fi = 2 * I + v;
+        if (fi < 0 || fi >= Mf) continue;
+        s += (u ? 0.5 : 1.0) * (v ? 0.5 : 1.0) * rf[(size_t)fj * Mf + fi];
+      }
+    }
+    bc[k] = s;
+  }
+}
+// x_f += P x_c on the active fine nodes
+__global__ void k_q1p(int nxc, int nyc, const unsigned char* __restrict__ q1af, const double* __restrict__ xc, double* __restrict__ xf) {
+  const int Mc = nxc + 1, Mf = 2 * nxc + 1;
+  const size_t n1f = (size_t)Mf * (2 * nyc + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1f; k += (size_t)gridDim.x * blockDim.x) {
+    if (!q1af[k]) continue;
+    const int j = (int)(k / Mf), i = (int)(k - (size_t)j * Mf);
+    const int I0 = i >> 1, J0 = j >> 1, I1 = (i & 1) ? I0 + 1 : I0, J1 = (j & 1) ? J0 + 1 : J0;
+    const double wx = (i & 1) ? 0.5 : 1.0, wy = (j & 1) ? 0.5 : 1.0;
+    double s = wx * wy * xc[(size_t)J0 * Mc + I0];
+    if (i & 1) s += wx * wy * xc[(size_t)J0 * Mc + I1];
+    if (j & 1) s += wx * wy * xc[(size_t)J1 * Mc + I0];
+    if ((i & 1) && (j & 1)) s += wx * wy * xc[(size_t)J1 * Mc + I1];
+    xf[k] += s;
+  }
+}
+// level right-hand side b = v (0 on inactive nodes) and x = omega D^{-1} b
+__global__ void k_q1j0(size_t m, const unsigned char* __restrict__ q1a, const double* __restrict__ d, double omega,
+                       const double* __restrict__ v, double* __restrict__ b, double* __restrict__ x) {
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
+    const double bv = q1a[k] ? v[k] : 0.0;
+    b[k] = bv;
+    x[k] = omega * d[k] * bv;
+  }
+}
+// coarsest level: x = A_c^+ b over the active nodes (column-major)
+__global__ void k_q1dense(int m, const int* __restrict__ idx, const double* __restrict__ Ainv, const double* __restrict__ b,
+                          double* __restrict__ x) {
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < m; r += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < m; ++k) s += Ainv[(size_t)k * m + r] * b[idx[k]];
+    x[idx[r]] = s;
+  }
+}
+// Q0 elimination of M_Q [x1; x0] = [r1; r0]: t_I = r1_I - (1/4) sum_{active T around I} r0_T
+// on active Q1 nodes (R = |T|/4, Q0 = |T|), 0 elsewhere
+__global__ void k_mq_elim(int nx, int ny, const unsigned char* __restrict__ act, const unsigned char* __restrict__ q1a,
+                          const double* __restrict__ r, double* __restrict__ t) {
+  const int M = nx + 1;
+  const size_t n1 = (size_t)M * (ny + 1);
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1; k += (size_t)gridDim.x * blockDim.x) {
+    if (!q1a[k]) { t[k] = 0.0; continue; }
+    const int J = (int)(k / M), I = (int)(k - (size_t)J * M);
+    double s = 0.0;
+    for (int dy = 0; dy < 2; ++dy)
+      for (int dx = 0; dx < 2; ++dx) {
+        const int ex = I - 1 + dx, ey = J - 1 + dy;
+        if (ex >= 0 && ex < nx && ey >= 0 && ey < ny && act[(size_t)ey * nx + ex]) s += r[n1 + (size_t)ey * nx + ex];
+      }
+    t[k] = r[k] - 0.25 * s;
+  }
+}
+// back substitution: z1 = x1, z0_T = r0_T / |T| - (1/4) sum_{I in T} x1_I (active);
+// inactive unknowns keep r (identity rows)
+__global__ void k_mq_back(int nx, int ny, double h, const unsigned char* __restrict__ act, const unsigned char* __restrict__ q1a,
+                          const double* __restrict__ x1, const double* __restrict__ r, double* __restrict__ z) {
+  const int M = nx + 1;
+  const size_t n1 = (size_t)M * (ny + 1), n0 = (size_t)nx * ny;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < n1 + n0; k += (size_t)gridDim.x * blockDim.x) {
+    if (k < n1) { z[k] = q1a[k] ? x1[k] : r[k]; continue; }
+    const size_t e = k - n1;
+    if (!act[e]) { z[k] = r[k]; continue; }
+    const int ex = (int)(e % nx), ey = (int)(e / nx);
+    const double s = x1[(size_t)ey * M + ex] + x1[(size_t)ey * M + ex + 1] + x1[(size_t)(ey + 1) * M + ex] +
+                     x1[(size_t)(ey + 1) * M + ex + 1];
+    z[k] = r[k] / (h * h) - 0.25 * s;
+  }
+}
+// CG with a given preconditioned residual z: p = z, rz = <r, z>
+__global__ void __launch_bounds__(RB) k_pcg2_start(size_t m, const double* __restrict__ r, const double* __restrict__ z,
+                                                   double* __restrict__ p, PcgS* st, Slot sl) {
+  double v[1] = {0.0};
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
+    p[k] = z[k];
+    v[0] += r[k] * z[k];
+  }
+  if (slot_arrive<1>(sl, blockIdx.x, v)) {
+    st->rz = v[0]; st->its = 0; st->alpha = 0; st->beta = 0;
+    st->done = v[0] > 0.0 ? 0 : 1;
+  }
+}
+// x += alpha p, r -= alpha q
+__global__ void k_pcg2_xr(size_t m, const double* __restrict__ p, const double* __restrict__ q, double* __restrict__ x,
+                          double* __restrict__ r, PcgS* st) {
+  if (st->done) return;
+  const double al = st->alpha;
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) {
+    x[k] += al * p[k];
+    r[k] -= al * q[k];
+  }
+}
+// beta = <r, z>_new / <r, z>
+__global__ void __launch_bounds__(RB) k_pcg2_beta(size_t m, const double* __restrict__ r, const double* __restrict__ z, PcgS* st,
+                                                  Slot sl) {
+  if (st->done) return;
+  double v[1] = {0.0};
+  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < m; k += (size_t)gridDim.x * blockDim.x) v[0] += r[k] * z[k];
+  if (slot_arrive<1>(sl, blockIdx.x, v)) {
+    if (v[0] > 0.0) { st->beta = v[0] / st->rz; st->rz = v[0]; st->its += 1; }
+    else st->done = 1;
+  }
+}
+
+// host: build the two Q1 hierarchies on the velocity levels' element masks
+static eth_status q_build(G* g) {
+  for (int w = 0; w < 2; ++w) {
+    QHier& Q = g->qh[w];
+    const double shift = (w == 0 && g->outflow) ? Q1_SHIFT : 0.0;
+    Q.shift = shift;
+    for (const MLev& V : g->lv) {
+      QLev L;
+      L.nx = V.nx; L.ny = V.ny;
+      L.n1 = (size_t)(V.nx + 1) * (V.ny + 1);
+      L.act = V.act;
+      std::vector<unsigned char> fix, dir, q1a;
+      node_roles(V.nx, V.ny, g->outflow, V.hact, fix, dir, q1a);
+      L.hq1a = q1a;
+      ETH_CUDA(cudaMalloc((void**)&L.q1a, L.n1));
+      ETH_CUDA(cudaMemcpy(L.q1a, q1a.data(), L.n1, cudaMemcpyHostToDevice));
+      for (double** p : {&L.d, &L.x, &L.b, &L.r}) {
+        ETH_CUDA(cudaMalloc((void**)p, L.n1 * sizeof(double)));
+        ETH_CUDA(cudaMemset(*p, 0, L.n1 * sizeof(double)));
+      }
+      k_k1dinv<<<nblk(L.n1), 256, 0, g->s>>>(L.nx, L.ny, shift, L.act, L.q1a, L.d);
+      ETH_CUDA(cudaGetLastError());
+      Q.lv.push_back(L);
+    }
+    // coarsest: dense (pseudo-)inverse over the active nodes
+    const QLev& C = Q.lv.back();
+    const MLev& CV = g->lv.back();
+    std::vector<int> idx, pos(C.n1, -1);
+    for (size_t k = 0; k < C.n1; ++k)
+      if (C.hq1a[k]) { pos[k] = (int)idx.size(); idx.push_back((int)k); }
+    const int m = (int)idx.size();
+    std::vector<double> A((size_t)m * m, 0.0);
+    const int M = C.nx + 1;
+    for (int ey = 0; ey < C.ny; ++ey)
+      for (int ex = 0; ex < C.nx; ++ex) {
+        if (!CV.hact[(size_t)ey * C.nx + ex]) continue;
+        for (int li = 0; li < 4; ++li)
+          for (int lj = 0; lj < 4; ++lj) {
+            const int ri = pos[(size_t)(ey + (li >> 1)) * M + ex + (li & 1)], cj = pos[(size_t)(ey + (lj >> 1)) * M + ex + (lj & 1)];
+            A[(size_t)ri * m + cj] += q1k(li & 1, lj & 1) * q1m(li >> 1, lj >> 1) + q1m(li & 1, lj & 1) * q1k(li >> 1, lj >> 1);
+          }
+      }
+    if (shift > 0.0)
+      for (int k = 0; k < m; ++k)
+        if (idx[k] % M == C.nx) A[(size_t)k * m + k] += shift;
+    if (shift == 0.0)   // singular on the constants: (A + e e^T)^{-1} - e e^T, e = 1/sqrt(m)
+      for (size_t k = 0; k < A.size(); ++k) A[k] += 1.0 / m;
+    if (!invert_dense(A, m)) { set_error("masked grid: singular coarsest Q1 operator"); return ETH_EINVAL; }
+    if (shift == 0.0)
+      for (size_t k = 0; k < A.size(); ++k) A[k] -= 1.0 / m;
+    std::vector<double> Ac((size_t)m * m);
+    for (int r = 0; r < m; ++r)
+      for (int k = 0; k < m; ++k) Ac[(size_t)k * m + r] = A[(size_t)r * m + k];
+    Q.ncf = m;
+    ETH_CUDA(cudaMalloc((void**)&Q.cidx, std::max(1, m) * sizeof(int)));
+    ETH_CUDA(cudaMalloc((void**)&Q.cinv, std::max<size_t>(1, Ac.size()) * sizeof(double)));
+    ETH_CUDA(cudaMemcpy(Q.cidx, idx.data(), m * sizeof(int), cudaMemcpyHostToDevice));
+    ETH_CUDA(cudaMemcpy(Q.cinv, Ac.data(), Ac.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return ETH_OK;
+}
+
+// z = V(r): one V-cycle of hierarchy w (V(1,1), damped Jacobi); z may alias nothing of the hierarchy
+static eth_status qvcycle(G* g, int w, const double* r, double* z) {
+  QHier& Q = g->qh[w];
+  const int nl = (int)Q.lv.size();
+  const double sh = Q.shift, om = Q1_OMEGA;
+  {
+    QLev& L = Q.lv[0];
+    k_q1j0<<<nblk(L.n1), 256, 0, g->s>>>(L.n1, L.q1a, L.d, om, r, L.b, L.x);
+    g->launches++;
+  }
+  for (int l = 0; l < nl - 1; ++l) {
+    QLev& L = Q.lv[l];
+    QLev& C = Q.lv[l + 1];
+    k_k1node<<<nblk(L.n1), 256, 0, g->s>>>(L.nx, L.ny, 1, sh, L.act, L.q1a, L.x, L.b, L.d, om, L.r);
+    k_q1r<<<nblk(C.n1), 256, 0, g->s>>>(C.nx, C.ny, C.q1a, L.r, C.b);
+    if (l + 1 < nl - 1) k_q1j0<<<nblk(C.n1), 256, 0, g->s>>>(C.n1, C.q1a, C.d, om, C.b, C.b, C.x);
+    g->launches += 3;
+  }
+  {
+    QLev& C = Q.lv[nl - 1];
+    ETH_CUDA(cudaMemsetAsync(C.x, 0, C.n1 * sizeof(double), g->s));
+    k_q1dense<<<cdiv(Q.ncf, 128), 128, 0, g->s>>>(Q.ncf, Q.cidx, Q.cinv, C.b, C.x);
+    g->launches++;
+  }
+  for (int l = nl - 2; l >= 0; --l) {
+    QLev& L = Q.lv[l];
+    const QLev& C = Q.lv[l + 1];
+    k_q1p<<<nblk(L.n1), 256, 0, g->s>>>(C.nx, C.ny, L.q1a, C.x, L.x);
+    k_k1node<<<nblk(L.n1), 256, 0, g->s>>>(L.nx, L.ny, 2, sh, L.act, L.q1a, L.x, L.b, L.d, om, l == 0 ? z : L.r);
+    if (l > 0) std::swap(L.x, L.r);
+    g->launches += 2;
+  }
+  if (nl == 1) ETH_CUDA(cudaMemcpyAsync(z, Q.lv[0].x, Q.lv[0].n1 * sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaGetLastError());
+  return ETH_OK;
+}
+
+}  // namespace msk
+}  // namespace eth
+
+// ---------------------------------------------------------------------------
 // pressure solves and the block-triangular preconditioners
 // ---------------------------------------------------------------------------
 namespace eth {
 namespace msk {
 
-constexpr double AP_RTOL = 1e-6;    // inner PCG on Ap (relative residual)
-constexpr int AP_MAXIT = 4000;
-constexpr double MQ_RTOL = 1e-8;    // inner PCG on M_Q
-constexpr int MQ_MAXIT = 1000;
+constexpr int AP_ITS = 3;           // CG steps on Ap (Q1 V-cycle preconditioner)
+constexpr int MQ_ITS = 3;           // CG steps on the Schur complement of M_Q (Q1 V-cycle preconditioner)
 constexpr int Q1_CHEB = 10;         // Chebyshev steps of the Q1 mass solve
-constexpr int PCG_CHECK = 8;        // host convergence check every PCG_CHECK steps
 
 // Chebyshev semi-iteration on D^{-1} Q (spectrum in [1/4, 9/4] for the Q1 mass
 // matrix on squares, element-wise bound, identity rows included)
@@ -1299,7 +1523,7 @@ static eth_status q1_mass_inv(G* g, const double* b, double* x) {
   double rho = 1.0 / sigma;
   for (int k = 0; k < Q1_CHEB; ++k) {
     const double rn = 1.0 / (2.0 * sigma - rho);
-    k_q1apply<<<nblk(m), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->q1a, nullptr, d, q);
+    k_q1apply<<<nblk(m), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->q1a, nullptr, 0.0, d, q);
     k_cheb_upd<<<nblk(m), 256, 0, g->s>>>(m, rn * rho, 2.0 * rn / delta, d, q, g->q1dinv, x, r, dn);
     ETH_CUDA(cudaGetLastError());
     g->launches += 2;
@@ -1317,57 +1541,57 @@ static eth_status ap_apply(G* g, const double* p, double* q) {
   return pgat64(g, P_PIN, g->n1, p, q);
 }
 
-// Jacobi-preconditioned CG on (Ap + pin) x = b (op 0, N_1) or (M_Q + pin) x = b
-// (op 1, N_1 + N_0, with k projected out of b and x); scalars stay on the
-// device, the host looks at the convergence flag every PCG_CHECK steps.
-static eth_status pcg(G* g, int op, const double* b, double* x, double rtol, int maxit) {
-  const size_t m = op == 0 ? g->n1 : g->np;
-  const double* dinv = op == 0 ? g->apdinv : g->mqdinv;
-  const double* kv = op == 0 ? nullptr : g->kv;
+// x ~= A^{-1} b by `its` CG steps preconditioned with one Q1 V-cycle: op 0 A = Ap
+// + pin (V-cycle of the Q1 Laplacian with the outflow shift), op 1 A = S + pin,
+// S = Qk - R^T Q0^{-1} R (V-cycle of the natural-boundary Q1 Laplacian; b and
+// the result are defined up to constants).  A fixed step count, scalars on the
+// device: no host synchronisation.
+static eth_status pcg_mg(G* g, int op, const double* b, double* x, int its) {
+  const size_t m = g->n1;
   const int nb = rblocks(m);
-  if (kv) ETH_TRY(dot2(g, m, kv, b, nullptr, nullptr, 0));
-  k_pcg_init<<<nb, RB, 0, g->s>>>(m, b, kv, g->red, g->kk, dinv, g->pr, g->pz, g->pp, x, g->pcg, rtol * rtol, slot(g, nb));
-  ETH_CUDA(cudaGetLastError());
+  double *r = g->pr, *z = g->pz, *p = g->pp, *q = g->pq;
+  ETH_CUDA(cudaMemcpyAsync(r, b, m * sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+  ETH_CUDA(cudaMemsetAsync(x, 0, m * sizeof(double), g->s));
+  ETH_TRY(qvcycle(g, op, r, z));
+  k_pcg2_start<<<nb, RB, 0, g->s>>>(m, r, z, p, g->pcg, slot(g, nb));
   g->launches++;
-  for (int it = 0; it < maxit; ++it) {
-    if (op == 0) ETH_TRY(ap_apply(g, g->pp, g->pq));
+  for (int it = 0; it < its; ++it) {
+    if (op == 0) ETH_TRY(ap_apply(g, p, q));
     else {
-      k_mq_apply<<<nblk(m), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->q1a, 1, g->pp, g->pq);
-      ETH_CUDA(cudaGetLastError());
+      k_q1apply<<<nblk(m), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->q1a, nullptr, -1.0 / 16.0, p, q);
       g->launches++;
     }
-    k_pcg_alpha<<<nb, RB, 0, g->s>>>(m, g->pp, g->pq, g->pcg, slot(g, nb));
-    k_pcg_xr<<<nb, RB, 0, g->s>>>(m, g->pp, g->pq, dinv, x, g->pr, g->pz, g->pcg, slot(g, nb));
-    k_pcg_p<<<nblk(m), 256, 0, g->s>>>(m, g->pz, g->pp, g->pcg);
-    ETH_CUDA(cudaGetLastError());
-    g->launches += 3;
-    if ((it + 1) % PCG_CHECK == 0 || it + 1 == maxit) {
-      ETH_CUDA(cudaMemcpyAsync(g->pcgh, g->pcg, sizeof(PcgS), cudaMemcpyDeviceToHost, g->s));
-      ETH_CUDA(cudaStreamSynchronize(g->s));
-      if (g->pcgh->done) break;
-    }
+    k_pcg_alpha<<<nb, RB, 0, g->s>>>(m, p, q, g->pcg, slot(g, nb));
+    k_pcg2_xr<<<nblk(m), 256, 0, g->s>>>(m, p, q, x, r, g->pcg);
+    g->launches += 2;
+    if (it + 1 == its) break;
+    ETH_TRY(qvcycle(g, op, r, z));
+    k_pcg2_beta<<<nb, RB, 0, g->s>>>(m, r, z, g->pcg, slot(g, nb));
+    k_pcg_p<<<nblk(m), 256, 0, g->s>>>(m, z, p, g->pcg);
+    g->launches += 2;
   }
-  g->pcg_its += g->pcgh->its;
-  if (kv) {
-    ETH_TRY(dot2(g, m, kv, x, nullptr, nullptr, 0));
-    k_proj<<<nblk(m), 256, 0, g->s>>>(m, x, kv, g->red, g->kk, x);
-    ETH_CUDA(cudaGetLastError());
-    g->launches++;
-  }
+  ETH_CUDA(cudaGetLastError());
   return ETH_OK;
 }
 
 // Step I (reduced system [u; p1]): z_p = -M_S^{-1} r_p = -Ap^{-1} F1 Q1^{-1} r_p,
 // z_u = V(r_u - B1^T z_p)  (Sec. 3.1, Eq. discrete-commutator1x)
+// Without a wind (the Stokes step) F1 = nu K1 annihilates the constants while the
+// outflow Schur complement does not: there the Stokes limit of the commutator,
+// F1 = nu Ap, gives M_S^{-1} = nu Q1^{-1}.
 static eth_status prec_pcd(G* g, const eth_opts* o, const double* r, double* z) {
   const double* rp = r + g->nu2;
   double* zp = z + g->nu2;
   ETH_TRY(q1_mass_inv(g, rp, g->pa));
-  k_q1apply<<<nblk(g->n1), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->q1a, g->f1e, g->pa, g->pb);
-  ETH_CUDA(cudaGetLastError());
-  g->launches++;
-  ETH_TRY(pcg(g, 0, g->pb, g->px, AP_RTOL, AP_MAXIT));
-  k_scale<<<nblk(g->n1), 256, 0, g->s>>>(g->n1, -1.0, g->px, zp);
+  if (g->conv) {
+    k_q1apply<<<nblk(g->n1), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->q1a, g->f1e, 0.0, g->pa, g->pb);
+    ETH_CUDA(cudaGetLastError());
+    g->launches++;
+    ETH_TRY(pcg_mg(g, 0, g->pb, g->px, AP_ITS));
+    k_scale<<<nblk(g->n1), 256, 0, g->s>>>(g->n1, -1.0, g->px, zp);
+  } else {
+    k_scale<<<nblk(g->n1), 256, 0, g->s>>>(g->n1, -g->nu, g->pa, zp);
+  }
   ETH_CUDA(cudaGetLastError());
   g->launches++;
   ETH_TRY(bsub(g, false, r, zp, g->t0));
@@ -1376,12 +1600,24 @@ static eth_status prec_pcd(G* g, const eth_opts* o, const double* r, double* z) 
 
 // Step II (full system): z_p = -nu M_Q^+ r_p (k projected out), z_u = V(r_u - B^T z_p)
 // (Sec. 3.1, the preconditioner M_1 of Eq. nse-precon-ref)
+// M_Q^+ r_p: k projected out of r_p, Q0 eliminated, CG on the Schur complement,
+// back substitution, k projected out of the result.
 static eth_status prec_m1(G* g, const eth_opts* o, const double* r, double* z) {
   double* zp = z + g->nu2;
-  ETH_TRY(pcg(g, 1, r + g->nu2, g->px, MQ_RTOL, MQ_MAXIT));
-  k_scale<<<nblk(g->np), 256, 0, g->s>>>(g->np, -g->nu, g->px, zp);
+  const double* rp = r + g->nu2;
+  ETH_TRY(dot2(g, g->np, g->kv, rp, nullptr, nullptr, 4));
+  k_proj<<<nblk(g->np), 256, 0, g->s>>>(g->np, rp, g->kv, g->red + 4, g->kk, g->pa);
+  k_mq_elim<<<nblk(g->n1), 256, 0, g->s>>>(g->nx, g->ny, g->act, g->q1a, g->pa, g->pb);
   ETH_CUDA(cudaGetLastError());
-  g->launches++;
+  g->launches += 2;
+  ETH_TRY(pcg_mg(g, 1, g->pb, g->px, MQ_ITS));
+  k_mq_back<<<nblk(g->np), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->q1a, g->px, g->pa, g->pb);
+  ETH_CUDA(cudaGetLastError());
+  ETH_TRY(dot2(g, g->np, g->kv, g->pb, nullptr, nullptr, 4));
+  k_proj<<<nblk(g->np), 256, 0, g->s>>>(g->np, g->pb, g->kv, g->red + 4, g->kk, g->pb);
+  k_scale<<<nblk(g->np), 256, 0, g->s>>>(g->np, -g->nu, g->pb, zp);
+  ETH_CUDA(cudaGetLastError());
+  g->launches += 3;
   ETH_TRY(bsub(g, true, r, zp, g->t0));
   return vcycle(g, g->t0, z, std::max(1, o->mg_pre), std::max(1, o->mg_post), (float)(o->mg_omega > 0 ? o->mg_omega : 0.85));
 }
@@ -1531,7 +1767,6 @@ static eth_status two_stage(G* g, const eth_opts* o, const double* b, double* x,
   const int maxit = o->maxit > 0 ? o->maxit : 2000;
   ETH_TRY(gm_alloc(g, restart));
   ETH_TRY(prepare(g));
-  g->pcg_its = 0;
   const size_t nred = g->nu2 + g->n1;
   k_x0<<<nblk(g->nt), 256, 0, g->s>>>(g->nv, g->np, g->fix, b, x);
   ETH_CUDA(cudaGetLastError());
@@ -1594,10 +1829,9 @@ static void mgrid_free(eth_mgrid* g) {
   cudaFree(g->act); cudaFree(g->fix); cudaFree(g->q1a); cudaFree(g->wind); cudaFree(g->E);
   cudaFree(g->part); cudaFree(g->ticket); cudaFree(g->red);
   if (g->redh) cudaFreeHost(g->redh);
-  if (g->pcgh) cudaFreeHost(g->pcgh);
   if (g->hh) cudaFreeHost(g->hh);
   cudaFree(g->pcg);
-  cudaFree(g->mdinv); cudaFree(g->q1dinv); cudaFree(g->mqdinv); cudaFree(g->apdinv); cudaFree(g->kv); cudaFree(g->f1e);
+  cudaFree(g->mdinv); cudaFree(g->q1dinv); cudaFree(g->kv); cudaFree(g->f1e);
   cudaFree(g->t0); cudaFree(g->t1); cudaFree(g->t2); cudaFree(g->xs); cudaFree(g->bv);
   cudaFree(g->pr); cudaFree(g->pz); cudaFree(g->pp); cudaFree(g->pq); cudaFree(g->px); cudaFree(g->pa); cudaFree(g->pb);
   cudaFree(g->V); cudaFree(g->Z); cudaFree(g->hd); cudaFree(g->hd2); cudaFree(g->yd); cudaFree(g->mpart);
@@ -1630,27 +1864,23 @@ static eth_status mgrid_init(eth_mgrid* g, const unsigned char* active) {
   ETH_CUDA(A((void**)&g->red, 64 * 8));
   ETH_CUDA(cudaMallocHost((void**)&g->redh, 64 * 8));
   ETH_CUDA(A((void**)&g->pcg, sizeof(PcgS)));
-  ETH_CUDA(cudaMallocHost((void**)&g->pcgh, sizeof(PcgS)));
-  std::memset(g->pcgh, 0, sizeof(PcgS));
   ETH_CUDA(A((void**)&g->mdinv, g->nv * 8));
   ETH_CUDA(A((void**)&g->q1dinv, g->n1 * 8));
-  ETH_CUDA(A((void**)&g->apdinv, g->n1 * 8));
-  ETH_CUDA(A((void**)&g->mqdinv, g->np * 8));
   ETH_CUDA(A((void**)&g->kv, g->np * 8));
   ETH_CUDA(A((void**)&g->f1e, n0 * 16 * 8));
   for (double** p : {&g->t0, &g->t1, &g->t2, &g->xs, &g->bv}) ETH_CUDA(A((void**)p, g->nt * 8));
   for (double** p : {&g->pr, &g->pz, &g->pp, &g->pq, &g->px, &g->pa, &g->pb}) ETH_CUDA(A((void**)p, g->np * 8));
-  k_diag_setup<<<nblk(g->nv + g->np), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->fix, g->q1a, g->mdinv, g->q1dinv, g->mqdinv,
-                                                       g->kv);
-  ETH_CUDA(cudaGetLastError());
-  k_ap_diag<<<nblk(g->n1), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->q1a, g->mdinv, g->apdinv);
+  k_diag_setup<<<nblk(g->nv + g->np), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->fix, g->q1a, g->mdinv, g->q1dinv, g->kv);
   ETH_CUDA(cudaGetLastError());
   size_t cnt = 0;
   for (unsigned char v : g->h_q1a) cnt += v;
   for (unsigned char v : g->h_act) cnt += v;
   g->kk = (double)cnt;
   ETH_CUDA(cudaStreamSynchronize(g->s));
-  return mg_build_geometry(g);
+  ETH_TRY(mg_build_geometry(g));
+  ETH_TRY(q_build(g));
+  ETH_CUDA(cudaStreamSynchronize(g->s));
+  return ETH_OK;
 }
 
 extern "C" {
