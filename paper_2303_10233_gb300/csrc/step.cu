@@ -859,6 +859,14 @@ struct eth_mgrid {
   double *V = nullptr, *Z = nullptr, *hd = nullptr, *hd2 = nullptr, *yd = nullptr, *hh = nullptr, *mpart = nullptr;
   int gm_m = 0;                 // restart length the GMRES workspace holds
   double* bv = nullptr;         // right-hand side buffer of the Picard iteration (N_t)
+  double* zo = nullptr;         // preconditioned vector of the captured Arnoldi step (N_t)
+  cudaStream_t si = nullptr;    // internal stream of the solver (capturable)
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  // captured "z = P^{-1} v, w = K z" of each stage (v in xs, z in zo, w in t2) and the
+  // launch parameters they were captured with
+  cudaGraphExec_t gx[2] = {nullptr, nullptr};
+  double gsig[2][5] = {{0}};
+  long gnodes[2] = {0, 0};       // nodes of each captured graph
   long launches = 0;
 };
 
@@ -1680,6 +1688,40 @@ static eth_status cgs_pass(G* g, size_t n, int nvec, double* w, bool second) {
   return ETH_OK;
 }
 
+// The preconditioner and operator of one Arnoldi step (xs -> zo -> t2) as a CUDA
+// graph, captured at first use and again whenever a launch parameter baked into
+// it (wind on/off, nu, smoother damping and sweeps) changes; every buffer it
+// touches keeps its address for the life of the handle.
+static eth_status step_graph(G* g, const eth_opts* o, int stage) {
+  const int k = stage - 1;
+  const double sig[5] = {g->conv ? 1.0 : 0.0, g->nu, o->mg_omega, (double)o->mg_pre, (double)o->mg_post};
+  if (g->gx[k] && std::memcmp(sig, g->gsig[k], sizeof(sig)) != 0) {
+    cudaGraphExecDestroy(g->gx[k]);
+    g->gx[k] = nullptr;
+  }
+  if (!g->gx[k]) {
+    cudaGraph_t graph = nullptr;
+    ETH_CUDA(cudaStreamBeginCapture(g->s, cudaStreamCaptureModeThreadLocal));
+    const long l0 = g->launches;
+    eth_status st = sys_prec(g, o, stage, g->xs, g->zo);
+    if (st == ETH_OK) st = sys_apply(g, stage, g->zo, g->t2);
+    const cudaError_t ce = cudaStreamEndCapture(g->s, &graph);
+    g->launches = l0;
+    if (st != ETH_OK) { if (graph) cudaGraphDestroy(graph); return st; }
+    if (ce != cudaSuccess) return cuda_status(ce, "masked grid: graph capture");
+    const cudaError_t ie = cudaGraphInstantiate(&g->gx[k], graph, 0);
+    size_t nodes = 0;
+    cudaGraphGetNodes(graph, nullptr, &nodes);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return cuda_status(ie, "masked grid: graph instantiation");
+    g->gnodes[k] = (long)nodes;
+    std::memcpy(g->gsig[k], sig, sizeof(sig));
+  }
+  ETH_CUDA(cudaGraphLaunch(g->gx[k], g->s));
+  g->launches += g->gnodes[k];
+  return ETH_OK;
+}
+
 // Restarted right-preconditioned flexible GMRES on the stage's system (n
 // unknowns) from x; stops when the residual norm is <= tol_abs (the true
 // residual, recomputed at every restart) or after maxit iterations.
@@ -1706,8 +1748,14 @@ static eth_status gmres(G* g, const eth_opts* o, int stage, size_t n, const doub
     for (int j = 0; j < m; ++j) {
       double* vj = g->V + (size_t)j * ld;
       double* zj = g->Z + (size_t)j * ld;
-      ETH_TRY(sys_prec(g, o, stage, vj, zj));
-      ETH_TRY(sys_apply(g, stage, zj, r));   // r: the new direction w
+      if (o->graph) {   // z_j = P^{-1} v_j and w = K z_j by one graph launch (staged through xs / zo)
+        ETH_CUDA(cudaMemcpyAsync(g->xs, vj, n * sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+        ETH_TRY(step_graph(g, o, stage));
+        ETH_CUDA(cudaMemcpyAsync(zj, g->zo, n * sizeof(double), cudaMemcpyDeviceToDevice, g->s));
+      } else {
+        ETH_TRY(sys_prec(g, o, stage, vj, zj));
+        ETH_TRY(sys_apply(g, stage, zj, r));   // r: the new direction w
+      }
       ETH_TRY(cgs_pass(g, n, j + 1, r, false));
       ETH_TRY(cgs_pass(g, n, j + 1, r, true));
       k_mdot<<<dim3(MD_NB, 1), RB, 0, g->s>>>(n, r, ld, r, g->mpart);
@@ -1834,7 +1882,12 @@ static void mgrid_free(eth_mgrid* g) {
   cudaFree(g->mdinv); cudaFree(g->q1dinv); cudaFree(g->kv); cudaFree(g->f1e);
   cudaFree(g->t0); cudaFree(g->t1); cudaFree(g->t2); cudaFree(g->xs); cudaFree(g->bv);
   cudaFree(g->pr); cudaFree(g->pz); cudaFree(g->pp); cudaFree(g->pq); cudaFree(g->px); cudaFree(g->pa); cudaFree(g->pb);
-  cudaFree(g->V); cudaFree(g->Z); cudaFree(g->hd); cudaFree(g->hd2); cudaFree(g->yd); cudaFree(g->mpart);
+  cudaFree(g->V); cudaFree(g->Z); cudaFree(g->hd); cudaFree(g->hd2); cudaFree(g->yd); cudaFree(g->mpart); cudaFree(g->zo);
+  for (cudaGraphExec_t& e : g->gx)
+    if (e) cudaGraphExecDestroy(e);
+  for (cudaEvent_t& e : g->ev)
+    if (e) cudaEventDestroy(e);
+  if (g->si) cudaStreamDestroy(g->si);
   delete g;
 }
 
@@ -1868,7 +1921,9 @@ static eth_status mgrid_init(eth_mgrid* g, const unsigned char* active) {
   ETH_CUDA(A((void**)&g->q1dinv, g->n1 * 8));
   ETH_CUDA(A((void**)&g->kv, g->np * 8));
   ETH_CUDA(A((void**)&g->f1e, n0 * 16 * 8));
-  for (double** p : {&g->t0, &g->t1, &g->t2, &g->xs, &g->bv}) ETH_CUDA(A((void**)p, g->nt * 8));
+  for (double** p : {&g->t0, &g->t1, &g->t2, &g->xs, &g->bv, &g->zo}) ETH_CUDA(A((void**)p, g->nt * 8));
+  ETH_CUDA(cudaStreamCreateWithFlags(&g->si, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : g->ev) ETH_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   for (double** p : {&g->pr, &g->pz, &g->pp, &g->pq, &g->px, &g->pa, &g->pb}) ETH_CUDA(A((void**)p, g->np * 8));
   k_diag_setup<<<nblk(g->nv + g->np), 256, 0, g->s>>>(g->nx, g->ny, g->h, g->act, g->fix, g->q1a, g->mdinv, g->q1dinv, g->kv);
   ETH_CUDA(cudaGetLastError());
@@ -1990,11 +2045,21 @@ eth_status eth_mgrid_rhs(eth_mgrid* g, const double* ubc, double* b) {
   return pgat64(g, P_NEG, g->np, (const double*)nullptr, b + g->nu2);
 }
 
+// The solve runs on the handle's internal stream (capturable), after the work
+// already queued on the user stream, and is joined back to it.
 static eth_status mgrid_solve(eth_mgrid* g, const eth_opts* o, const double* b, double* x, eth_stats* st) {
   eth_stats tmp{};
   const long l0 = g->launches;
   const auto t0 = std::chrono::steady_clock::now();
-  ETH_TRY(two_stage(g, o, b, x, &tmp));
+  const cudaStream_t user = g->s;
+  ETH_CUDA(cudaEventRecord(g->ev[0], user));
+  ETH_CUDA(cudaStreamWaitEvent(g->si, g->ev[0], 0));
+  g->s = g->si;
+  const eth_status s2 = two_stage(g, o, b, x, &tmp);
+  g->s = user;
+  ETH_CUDA(cudaEventRecord(g->ev[1], g->si));
+  ETH_CUDA(cudaStreamWaitEvent(user, g->ev[1], 0));
+  if (s2 != ETH_OK) { cudaStreamSynchronize(g->si); return s2; }
   ETH_CUDA(cudaStreamSynchronize(g->s));
   tmp.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   tmp.kernel_launches = (int)(g->launches - l0);

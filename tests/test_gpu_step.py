@@ -193,3 +193,19 @@ def test_iterations_close_to_exact_blocks_and_mesh_independent(eth):
         assert g1 <= 3 * o1 + 5 and g2 <= 2 * o2 + 10, out
     # mesh independence: no growth from h = 1/2 to h = 1/8
     assert out[-1][3] <= out[0][3] + 4 and out[-1][4] <= out[0][4] + 8, out
+
+
+def test_graph_replay_matches_stream_launches(eth):
+    """The captured Arnoldi step (graph=1) gives bitwise the stream-launched solve."""
+    w = W.step(4)
+    g, G = _grids(eth, w)
+    s0 = step.StepSystem(g, w["nu"])
+    wind = s0.solve(s0.rhs(w["ubc"]))[: g.nu]
+    G.set_coefficients(w["nu"], _t(wind, G))
+    b = G.rhs(_t(w["ubc"], G))
+    x1, s1 = G.solve(b, tol=1e-8, graph=0)
+    x2, s2 = G.solve(b, tol=1e-8, graph=1)
+    x3, s3 = G.solve(b, tol=1e-8, graph=1)    # replay of the cached graphs
+    G.close()
+    assert s1["iters_total"] == s2["iters_total"] == s3["iters_total"]
+    assert torch.equal(x1, x2) and torch.equal(x2, x3)
