@@ -316,6 +316,8 @@ def run_ours(args):
     oseen = oseen_line(torch, eth, W, local)
     # ---- the uneven 64-instance batch, concurrent mixed vs plain FP64 one at a time
     batch = batch_line(torch, eth, W, local) if not args.no_batch else None
+    # ---- the flow over a step (masked grid, natural outflow), five Picard steps at h = 1/32
+    stepl = step_line(torch, eth, W, local, cpu=(ws == 1 and not args.no_cpu and rank == 0))
 
     # ---- roofline of the dominant kernel, timed live on the launching stream
     roof = roofline(G, torch, eth)
@@ -349,6 +351,7 @@ def run_ours(args):
         "roofline": roof,
         "oseen512": oseen,
         "batch64": batch,
+        "step": stepl,
         "cpu_baseline": cpu,
         "clocks": clocks,
         "wall_s": t_wall,
@@ -447,6 +450,52 @@ def batch_line(torch, eth, W, dev):
            "speedup_mixed_batched_vs_fp64": wall64 / wall}
     for G in grids:
         G.close()
+    return out
+
+
+def step_line(torch, eth, W, dev, m=32, cpu=True):
+    """The flow over a step (Sec. 3, Test problem 3) on the masked grid with h = 1/m
+    (m = 32: 11 m^2 = 11264 active squares, the paper's intermediate grid), nu = 1/50:
+    CUDA-event time of five Picard steps from the Stokes solution, each solved by the
+    two-stage PCD method to a 1e-6 true residual, after a warm-up run that captures
+    the Arnoldi-step graphs; iterations of both stages per step, nonlinear residuals,
+    N_t x iterations / time.  With cpu: the oracle's exact-block two-stage method on
+    the fifth (Oseen) system at h = 1/16, timed on the host (factorisations included)."""
+    w = W.step(m)
+    G = eth.MGrid(w["nx"], w["ny"], w["h"], w["x0"], w["y0"], w["active"], outflow=True, device=dev)
+    G.set_coefficients(w["nu"])
+    ub = torch.as_tensor(w["ubc"], dtype=torch.float64, device=G.device)
+    G.picard(ub, 5, tol=TOL)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    _, _, res, sts = G.picard(ub, 5, tol=TOL)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    its = sum(st["iters_total"] for st in sts)
+    out = {"workload": f"step_h1_{m}_nu0.02_picard5", "N_t": G.nt, "active_elements": int(w["active"].sum()),
+           "ms": ms, "iters": [[st["iters_stage1"], st["iters_stage2"]] for st in sts],
+           "relres": max(st["relres_true"] for st in sts), "status": [st["status"] for st in sts],
+           "nonlinear_residuals": res, "last_solve_ms": sts[-1]["seconds"] * 1e3,
+           "mdof_iter_s": G.nt * its / (ms / 1e3) / 1e6,
+           "gpu_launches": sum(st["kernel_launches"] for st in sts)}
+    G.close()
+    if cpu:
+        from oracle import step as ostep
+        mc = 16
+        wc = W.step(mc)
+        g = ostep.step_grid(mc)
+        xs, _ = ostep.picard(g, wc["nu"], wc["ubc"], 4)
+        s = ostep.StepSystem(g, wc["nu"], xs[-1][: g.nu])
+        b = s.rhs(wc["ubc"])
+        t = time.perf_counter()
+        _, info = ostep.two_stage(s, b, eta=TOL)
+        dt = time.perf_counter() - t
+        out["oracle_h1_16"] = {"N_t": g.nt, "s": dt, "iters": [info["its1"], info["its2"]],
+                               "mdof_iter_s": g.nt * (info["its1"] + info["its2"]) / dt / 1e6,
+                               "sample": "the fifth Picard system at h = 1/16 by the oracle's two-stage method with "
+                                         "exact (SuperLU) blocks, factorisations included"}
     return out
 
 
@@ -549,6 +598,23 @@ def profile_solve(n, kind):
     G.close()
 
 
+def profile_step(m):
+    """Two Picard steps (Stokes, then Oseen) on the step with h = 1/m, stream launches,
+    for an ncu launch list of the masked-grid solver (the Oseen solve's launches follow
+    the Stokes solve's)."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2303_10233_gb300 import eth, workloads as W
+    w = W.step(m)
+    G = eth.MGrid(w["nx"], w["ny"], w["h"], w["x0"], w["y0"], w["active"], outflow=True)
+    G.set_coefficients(w["nu"])
+    _, _, res, sts = G.picard(torch.as_tensor(w["ubc"], device="cuda"), 2, tol=TOL, graph=0)
+    print(f"profile_step m={m} its={[(s_['iters_stage1'], s_['iters_stage2']) for s_ in sts]} "
+          f"launches={[s_['kernel_launches'] for s_ in sts]}")
+    G.close()
+
+
 def est_table(nmax):
     """EST-MINRES inf-sup estimates on the lid-driven cavity for n = 16, 32, .., nmax
     (one JSON line per grid): MINRES iterations and the final gamma^2 estimate with
@@ -599,6 +665,8 @@ def main():
                     help="element rows per warp of the strip kernel in --profile-apply (0: the tile kernel)")
     ap.add_argument("--profile-solve", type=int, default=0, metavar="N",
                     help="only run two default solves on an N x N grid of --profile-kind (for ncu launch lists)")
+    ap.add_argument("--profile-step", type=int, default=0, metavar="M",
+                    help="two Picard steps of the step problem at h = 1/M for an ncu launch list")
     ap.add_argument("--est", type=int, default=0, metavar="N",
                     help="only print EST-MINRES inf-sup estimates on cavity grids 16 .. N")
     args = ap.parse_args()
@@ -610,6 +678,9 @@ def main():
         return
     if args.profile_solve:
         profile_solve(args.profile_solve, args.profile_kind)
+        return
+    if args.profile_step:
+        profile_step(args.profile_step)
         return
     if args.impl == "reference":
         run_reference(args)
