@@ -613,8 +613,13 @@ __device__ void cq2_residual_node(int n, T hx, T hy, T nu, const T* KM, const T*
   __syncthreads();
 }
 
+// Threads of the single-CTA coarse V-cycle: 1024 for the FP32 Stokes levels (64
+// registers, no spills), 512 where the convection terms need more registers.
 template <class T, int FL>
-__global__ void __launch_bounds__(512) k_q2_coarse_vc(CoarseQ2<T> L, const T* __restrict__ Ainv, int m,
+__host__ __device__ constexpr int q2_coarse_threads() { return (sizeof(T) == 4 && !(FL & QF_CONV)) ? 1024 : 512; }
+
+template <class T, int FL>
+__global__ void __launch_bounds__(q2_coarse_threads<T, FL>()) k_q2_coarse_vc(CoarseQ2<T> L, const T* __restrict__ Ainv, int m,
                                                         const T* __restrict__ bin, T* __restrict__ xout, T omega,
                                                         int pre, int post, const int* done, int ainv_smem) {
   ETH_GRID_DEP_WAIT();
@@ -1195,7 +1200,7 @@ static eth_status q2_coarse_launch(eth_grid* g, Hier<T>& H, int Lc, int pre, int
   static SmemAttr attr;   // largest dynamic shared memory enabled so far, per device
   if (smem > 200 * 1024) { set_error("multigrid: coarse levels exceed shared memory"); return ETH_EINVAL; }
   ETH_CUDA(smem_attr(k_q2_coarse_vc<T, FL>, smem, attr));
-  k_q2_coarse_vc<T, FL><<<1, 512, smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, pre, post, done,
+  k_q2_coarse_vc<T, FL><<<1, q2_coarse_threads<T, FL>(), smem, g->s>>>(C, H.coarse_inv, H.ncoarse, H.lv[Lc].b, H.lv[Lc].x, (T)H.omega, pre, post, done,
                                                   ainv_smem);
   ETH_CUDA(cudaGetLastError());
   g->launches++;
