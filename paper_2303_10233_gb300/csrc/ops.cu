@@ -2,6 +2,8 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <cstdio>
+#include <cstdlib>
 #include "ops.cuh"
 
 namespace eth {
@@ -167,32 +169,81 @@ eth_status tune_tiles(eth_grid* g, bool fp32) {
     auto it = g_tune_cache.find(key);
     if (it != g_tune_cache.end()) { g->tile_rows = it->second; g->tuned = true; return ETH_OK; }
   }
-  cudaEvent_t e0, e1;
+  // Each candidate is timed as a captured graph of REPS back-to-back launches on a
+  // private stream, the way the solvers replay it: timing stream launches would
+  // measure the host's launch rate (about 2 us per launch) for the small grids.
+  // Three rounds over all candidates, the minimum per candidate; a strip form
+  // within 10 % of the fastest wins the tie: inside the solvers' graphs, between
+  // the shared-memory-heavy multigrid kernels, the strip forms (no shared memory)
+  // measured relatively faster than alone (256^2 Stokes solve 5.83 ms with 2-row
+  // strips against 6.03 ms with 32 x 8 tiles, which alone time 14.2 and 13.4 us).
+  // ETH_TUNE_VERBOSE=1 in the environment prints every candidate's time.
+  cudaEvent_t e0, e1, ej;
+  cudaStream_t ts;
   ETH_CUDA(cudaEventCreate(&e0));
   ETH_CUDA(cudaEventCreate(&e1));
-  int best = TILE_STRIP + 8;
-  float best_ms = 1e30f;
+  ETH_CUDA(cudaEventCreateWithFlags(&ej, cudaEventDisableTiming));
+  ETH_CUDA(cudaStreamCreateWithFlags(&ts, cudaStreamNonBlocking));
+  ETH_CUDA(cudaEventRecord(ej, g->s));
+  ETH_CUDA(cudaStreamWaitEvent(ts, ej, 0));
+  const cudaStream_t keep = g->s;
+  g->s = ts;
   eth_status st = ETH_OK;
   const int cands[9] = {4, 8, 16, 8 + TILE_PERSIST, 2 + TILE_STRIP, 4 + TILE_STRIP, 6 + TILE_STRIP, 8 + TILE_STRIP, 16 + TILE_STRIP};
-  for (int ty : cands) {
+  constexpr int NC = 9, REPS = 16, ROUNDS = 3;
+  cudaGraphExec_t exec[NC] = {};
+  float tmin[NC];
+  for (int c = 0; c < NC; ++c) tmin[c] = 1e30f;
+  for (int c = 0; c < NC && st == ETH_OK; ++c) {
+    const int ty = cands[c];
     if (ty >= TILE_PERSIST && ty < TILE_STRIP && !fp32) continue;
     if (ty < TILE_PERSIST && q2_blocks(g->n, ty) > g->part_cap) continue;
     if (ty >= TILE_STRIP && q2s_blocks(g->n, ty - TILE_STRIP) > g->part_cap) continue;
     Slot s = make_slot(g, 11, 0);
-    for (int r = 0; r < 2 && st == ETH_OK; ++r) st = op_apply_tiles(g, fp32, g->b, g->tmp, s, ty);
+    for (int r = 0; r < 2 && st == ETH_OK; ++r) st = op_apply_tiles(g, fp32, g->b, g->tmp, s, ty);   // warm (attributes set)
     if (st != ETH_OK) break;
-    cudaEventRecord(e0, g->s);
-    constexpr int REPS = 6;
+    cudaGraph_t graph = nullptr;
+    cudaError_t ce = cudaStreamBeginCapture(ts, cudaStreamCaptureModeThreadLocal);
+    if (ce != cudaSuccess) { st = cuda_status(ce, "autotune capture"); break; }
     for (int r = 0; r < REPS && st == ETH_OK; ++r) st = op_apply_tiles(g, fp32, g->b, g->tmp, s, ty);
-    cudaEventRecord(e1, g->s);
-    if (st != ETH_OK) break;
-    if (cudaEventSynchronize(e1) != cudaSuccess) { st = cuda_status(cudaGetLastError(), "autotune"); break; }
-    float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
-    if (ms < best_ms) { best_ms = ms; best = ty; }
+    ce = cudaStreamEndCapture(ts, &graph);
+    if (st != ETH_OK) { if (graph) cudaGraphDestroy(graph); break; }
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec[c], graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { exec[c] = nullptr; st = cuda_status(ce, "autotune graph"); break; }
   }
+  for (int round = 0; round < ROUNDS && st == ETH_OK; ++round)
+    for (int c = 0; c < NC && st == ETH_OK; ++c) {
+      if (!exec[c]) continue;
+      cudaGraphLaunch(exec[c], ts);   // warm
+      cudaEventRecord(e0, ts);
+      for (int r = 0; r < 2; ++r) cudaGraphLaunch(exec[c], ts);
+      cudaEventRecord(e1, ts);
+      const cudaError_t ce = cudaEventSynchronize(e1);
+      if (ce != cudaSuccess) { st = cuda_status(ce, "autotune"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      tmin[c] = std::min(tmin[c], ms);
+      if (std::getenv("ETH_TUNE_VERBOSE"))
+        std::fprintf(stderr, "autotune n=%d fp32=%d code=%d us=%.3f\n", g->n, (int)fp32, cands[c], ms * 1e3 / (2 * REPS));
+    }
+  for (cudaGraphExec_t& e : exec)
+    if (e) cudaGraphExecDestroy(e);
+  int best = TILE_STRIP + 8;
+  float best_ms = 1e30f;
+  for (int c = 0; c < NC; ++c)
+    if (tmin[c] < best_ms) { best_ms = tmin[c]; best = cands[c]; }
+  if (best < TILE_STRIP)   // tie-break toward the strip forms
+    for (int c = 0; c < NC; ++c)
+      if (cands[c] >= TILE_STRIP && tmin[c] <= 1.10f * best_ms) { best = cands[c]; break; }
+  g->s = keep;
+  cudaEventRecord(ej, ts);
+  cudaStreamWaitEvent(keep, ej, 0);
+  cudaStreamSynchronize(ts);
+  cudaStreamDestroy(ts);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(ej);
   if (st != ETH_OK) return st;
   g->tile_rows = best;
   g->tuned = true;

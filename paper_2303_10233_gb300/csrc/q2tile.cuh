@@ -296,6 +296,17 @@ __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9
   }
 }
 
+// Resident CTAs per SM the register allocation must allow.  The FP32 operator
+// apply (32 x 8) is held to 5 CTAs without convection and 4 with it; the FP32
+// Stokes smoothing sweep with FP64 output and the fused dot (the V-cycle exit) to
+// 3: unbounded it takes 96 registers, 2 CTAs per SM, and the 333 tiles of a 256^2
+// level need a second wave on 152 SMs.
+template <class CT, int F, int EPI, int TY>
+__host__ __device__ constexpr int q2_min_blocks() {
+  return (TY == 8 && sizeof(CT) == 4 && EPI == EPI_APPLY) ? ((F & QF_CONV) ? 4 : 5)
+       : (TY == 8 && sizeof(CT) == 4 && EPI == EPI_SMOOTH && !(F & QF_CONV)) ? 3 : 1;
+}
+
 // TY = element rows per CTA (tile 32 x TY computed, 31 x (TY-1) owned); the
 // constants below shadow the default-shape ones of the namespace.
 // The FP32 operator apply (32 x 8) is held to 5 resident CTAs per SM without
@@ -304,7 +315,7 @@ __device__ __forceinline__ void q2_elem(const CT (&U)[2][9], const CT (&Wn)[2][9
 // 1024^2 57.9 -> 52.7 us; Oseen 1024^2 160 us at the 166 registers the
 // compiler takes unbounded -> 82 us).
 template <class TI, class TO, class CT, int F, int EPI, int TY = ETH_TEY>
-__global__ void __launch_bounds__(TEX * TY, (TY == 8 && EPI == EPI_APPLY && sizeof(CT) == 4) ? ((F & QF_CONV) ? 4 : 5) : 1)
+__global__ void __launch_bounds__(TEX * TY, q2_min_blocks<CT, F, EPI, TY>())
     k_q2(Q2Params<TI, TO, CT> P) {
   ETH_GRID_DEP_WAIT();
   constexpr int TEY = TY, OEY = TY - 1, Q2T = TEX * TY, SQY = 2 * TY + 1, SPY = TY + 1;
