@@ -121,12 +121,13 @@ __global__ void k_mc_xr(int m, const T* __restrict__ d, const T* __restrict__ q,
   }
 }
 
-// d = c1 d + c2 w
+// d = c1 d + c2 w (c1 = 0: d = c2 w without reading d, which may hold anything on the first step)
 template <class T>
 __global__ void k_mc_d(int m, T c1, T c2, const T* __restrict__ w, T* __restrict__ d, const int* done) {
   ETH_GRID_DEP_WAIT();
   if (done && *done) return;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x) d[k] = c1 * d[k] + c2 * w[k];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < m; k += gridDim.x * blockDim.x)
+    d[k] = (c1 == T(0) ? T(0) : c1 * d[k]) + c2 * w[k];
 }
 
 // k^T x = sum over Q1 - sum over P0 -> sl

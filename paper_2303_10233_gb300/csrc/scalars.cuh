@@ -57,7 +57,7 @@ enum : int {
   FIN_PCG_ALPHA,      // alpha = rz / <p, A p>
   FIN_PCG_RZ,         // beta = rz_new / rz; rz = rz_new
   FIN_PCG_RR,         // <r, r> <= target -> inner done
-  FIN_VWX,            // beta from the v sums; done = pending once the pending w/x update is applied
+  FIN_V,              // beta from the v sums (the w/x update runs in its own kernel, k_minres_wx)
 };
 
 __device__ __forceinline__ void finish_minres_gamma(Scalars* sc, double g2) {
@@ -126,12 +126,8 @@ __device__ __forceinline__ void finish_slot_n(const Slot& sl, const double (&s)[
     case FIN_VSUMS:
       v[S_BETA] = (s[0] - s[1]) / (v[S_NP1] + v[S_NP0]);
       break;
-    case FIN_VWX:
+    case FIN_V:
       v[S_BETA] = (s[0] - s[1]) / (v[S_NP1] + v[S_NP0]);
-      if (v[S_WXP] != 0.0) {
-        v[S_WXP] = 0.0;
-        if (v[S_PEND] != 0.0) sc->done = 1;
-      }
       sc->iter += 1;
       break;
     case FIN_MQ: {

@@ -25,6 +25,9 @@ static void work_free(void* p) {
   for (int k = 0; k < 2; ++k) { cudaFree(w->V[k]); cudaFree(w->Z[k]); cudaFree(w->W[k]); }
   if (w->gexec) cudaGraphExecDestroy(w->gexec);
   if (w->s2) cudaStreamDestroy(w->s2);
+  if (w->s3) cudaStreamDestroy(w->s3);
+  if (w->evw) cudaEventDestroy(w->evw);
+  if (w->evx) cudaEventDestroy(w->evx);
   if (w->sm) cudaStreamDestroy(w->sm);
   if (w->evu) cudaEventDestroy(w->evu);
   if (w->evf) cudaEventDestroy(w->evf);
@@ -57,6 +60,9 @@ eth_status work_get(eth_grid* g, Work** out) {
   double** bufs[] = {&w->x, &w->d, &w->r, &w->Kz, &w->bp, &w->V[0], &w->V[1], &w->Z[0], &w->Z[1], &w->W[0], &w->W[1]};
   for (double** b : bufs) ETH_CUDA(cudaMalloc((void**)b, nt * 8));
   ETH_CUDA(cudaStreamCreateWithFlags(&w->s2, cudaStreamNonBlocking));
+  ETH_CUDA(cudaStreamCreateWithFlags(&w->s3, cudaStreamNonBlocking));
+  ETH_CUDA(cudaEventCreateWithFlags(&w->evw, cudaEventDisableTiming));
+  ETH_CUDA(cudaEventCreateWithFlags(&w->evx, cudaEventDisableTiming));
   ETH_CUDA(cudaStreamCreateWithFlags(&w->sm, cudaStreamNonBlocking));
   ETH_CUDA(cudaEventCreateWithFlags(&w->evu, cudaEventDisableTiming));
   ETH_CUDA(cudaEventCreateWithFlags(&w->evf, cudaEventDisableTiming));
@@ -118,9 +124,16 @@ __global__ void k_set_boundary(int n, double* __restrict__ u, const double* __re
   }
 }
 
-// MINRES v_{j+1} = VA K z_j - VB v_j - VC v_{j-1} (into vo); sums of its p1/p0 blocks.
+// MINRES vector updates of iteration j, in two kernels so that the w/x part
+// leaves the critical path: k_minres_v, after the K apply, forms
+// v_{j+1} = VA K z_j - VB v_j - VC v_{j-1} (into vo) with the sums of its p1 / p0
+// blocks (FIN_V); k_minres_wx, beside the K apply on a second stream, applies the
+// update the previous Givens step left pending, w_j = WZ z_{j-1} - WO w_{j-2} -
+// WW w_{j-1} (into wold), x += XC w_j; k_minres_flags, after both, retires the
+// pending update and stops the loop once a converged step's update is applied.
+// Neither of the two concurrent kernels changes a flag the other reads.
 __global__ void k_minres_v(size_t nt, size_t nu2, size_t n1, const double* __restrict__ Kz, const double* __restrict__ vj,
-                           double* __restrict__ vo, const Scalars* __restrict__ sc, Slot sl) {
+                           double* __restrict__ vo, Scalars* __restrict__ sc, Slot sl) {
   ETH_GRID_DEP_WAIT();
   if (sc->done) return;
   const double a = sc->v[S_VA], b = sc->v[S_VB], c = sc->v[S_VC];
@@ -134,47 +147,25 @@ __global__ void k_minres_v(size_t nt, size_t nu2, size_t n1, const double* __res
   if (slot_arrive<2>(sl, blockIdx.x, v)) finish_slot_n<2>(sl, v);
 }
 
-// MINRES w_{j+1} = WZ z_j - WO w_{j-1} - WW w_j (into wo); x += XC w_{j+1}; last block: done = pending.
-__global__ void k_minres_wx(size_t nt, const double* __restrict__ zj, double* __restrict__ wo, const double* __restrict__ wj,
-                            double* __restrict__ x, Scalars* __restrict__ sc, Slot sl) {
+__global__ void k_minres_wx(size_t nt, const double* __restrict__ zprev, double* __restrict__ wold,
+                            const double* __restrict__ wcur, double* __restrict__ x, const Scalars* __restrict__ sc) {
   ETH_GRID_DEP_WAIT();
-  if (sc->done) return;
+  if (sc->done || sc->v[S_WXP] == 0.0) return;
   const double cz = sc->v[S_WZ], co = sc->v[S_WO], cw = sc->v[S_WW], cx = sc->v[S_XC];
   for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
-    const double w = cz * zj[k] - co * wo[k] - cw * wj[k];
-    wo[k] = w;
+    const double w = cz * zprev[k] - co * wold[k] - cw * wcur[k];
+    wold[k] = w;
     x[k] += cx * w;
   }
-  double v[1] = {0.0};
-  if (slot_arrive<1>(sl, blockIdx.x, v)) finish_slot(sl, 0.0);
 }
 
-// Fused MINRES vector update of iteration j: v_{j+1} = VA K z_j - VB v_j - VC v_{j-1}
-// (into vo, with the sums of its p1 / p0 blocks) and, when the previous Givens
-// step left it pending, its w/x update w_j = WZ z_{j-1} - WO w_{j-2} - WW w_{j-1}
-// (into wold), x += XC w_j.  The last block sets done once a converged step's
-// update has been applied.
-__global__ void k_minres_vwx(size_t nt, size_t nu2, size_t n1, const double* __restrict__ Kz, const double* __restrict__ vj,
-                             double* __restrict__ vo, const double* __restrict__ zprev, double* __restrict__ wold,
-                             const double* __restrict__ wcur, double* __restrict__ x, Scalars* __restrict__ sc, Slot sl) {
+__global__ void k_minres_flags(Scalars* sc) {
   ETH_GRID_DEP_WAIT();
   if (sc->done) return;
-  const double a = sc->v[S_VA], b = sc->v[S_VB], c = sc->v[S_VC];
-  const bool wx = sc->v[S_WXP] != 0.0;
-  const double cz = sc->v[S_WZ], co = sc->v[S_WO], cw = sc->v[S_WW], cx = sc->v[S_XC];
-  double a1 = 0.0, a0 = 0.0;
-  for (size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x; k < nt; k += (size_t)gridDim.x * blockDim.x) {
-    const double v = a * Kz[k] - b * vj[k] - c * vo[k];
-    vo[k] = v;
-    if (k >= nu2) { if (k < nu2 + n1) a1 += v; else a0 += v; }
-    if (wx) {
-      const double w = cz * zprev[k] - co * wold[k] - cw * wcur[k];
-      wold[k] = w;
-      x[k] += cx * w;
-    }
+  if (sc->v[S_WXP] != 0.0) {
+    sc->v[S_WXP] = 0.0;
+    if (sc->v[S_PEND] != 0.0) sc->done = 1;
   }
-  double v[2] = {a1, a0};
-  if (slot_arrive<2>(sl, blockIdx.x, v)) finish_slot_n<2>(sl, v);
 }
 
 // the w/x update left pending when the iteration loop stops (applied iff pending)
@@ -651,14 +642,22 @@ static eth_status minres_iter(eth_grid* g, Work* w, const eth_opts* o, bool fp32
   double* vo = w->V[(j + 1) & 1];
   double* wj = w->W[j & 1];
   double* wo = w->W[(j + 1) & 1];   // w_{j-2}, overwritten by w_j
-  ETH_TRY(op_apply_K_dot(g, fp32, false, zj, w->Kz, slot_of(g, SL_DELTA, 0, FIN_MINRES_DELTA), done));
   const int nb = vblocks(nt);
-  // v_{j+1} and the pending w/x update of iteration j-1 (z_{j-1} = zn's buffer, not yet overwritten)
-  k_minres_vwx<<<nb, 256, 0, g->s>>>(nt, nu2, (size_t)g->n1, w->Kz, vj, vo, zn, wj, wo, w->d, g->sc,
-                                     slot_of(g, SL_VSUM, nb, FIN_VWX));
+  // the pending w/x update of iteration j-1 (z_{j-1} = zn's buffer, not yet overwritten)
+  // on the side stream, beside the K apply and the v update
+  ETH_CUDA(cudaEventRecord(w->evw, g->s));
+  ETH_CUDA(cudaStreamWaitEvent(w->s3, w->evw, 0));
+  k_minres_wx<<<nb, 256, 0, w->s3>>>(nt, zn, wj, wo, w->d, g->sc);
+  ETH_CUDA(cudaGetLastError());
+  ETH_TRY(op_apply_K_dot(g, fp32, false, zj, w->Kz, slot_of(g, SL_DELTA, 0, FIN_MINRES_DELTA), done));
+  k_minres_v<<<nb, 256, 0, g->s>>>(nt, nu2, (size_t)g->n1, w->Kz, vj, vo, g->sc, slot_of(g, SL_VSUM, nb, FIN_V));
+  ETH_CUDA(cudaGetLastError());
+  ETH_CUDA(cudaEventRecord(w->evx, w->s3));
+  ETH_CUDA(cudaStreamWaitEvent(g->s, w->evx, 0));
+  k_minres_flags<<<1, 1, 0, g->s>>>(g->sc);
   ETH_CUDA(cudaGetLastError());
   ETH_TRY(precond_stokes<T>(g, w, o, vo, zn, FIN_MINRES_GAMMA, done));
-  g->launches += 1;
+  g->launches += 3;
   return ETH_OK;
 }
 

@@ -16,6 +16,8 @@ struct Work {
   double *x = nullptr, *d = nullptr, *r = nullptr, *Kz = nullptr, *bp = nullptr;
   double *V[2] = {nullptr, nullptr}, *Z[2] = {nullptr, nullptr}, *W[2] = {nullptr, nullptr};
   cudaStream_t s2 = nullptr;   // second branch (pressure block)
+  cudaStream_t s3 = nullptr;   // third branch (MINRES w/x update beside the K apply)
+  cudaEvent_t evw = nullptr, evx = nullptr;
   cudaStream_t sm = nullptr;   // internal main stream (capturable), joined to the user stream
   cudaEvent_t evf = nullptr, evj = nullptr, evu = nullptr, t0 = nullptr, t1 = nullptr;
   cudaGraphExec_t gexec = nullptr;
