@@ -352,6 +352,12 @@ eth_status eth_est_infsup(eth_grid* g, const double* delta_dev, const double* ga
 eth_status eth_mgrid_create(int nx, int ny, double h, double x0, double y0, const unsigned char* active_host,
                             int outflow, void* cuda_stream, eth_mgrid** out);
 void eth_mgrid_destroy(eth_mgrid* g);
+/* The node roles of a masked grid computed on the host alone (no device work):
+ * fixed_host and dirichlet_host receive N_v = (2nx+1)(2ny+1) bytes, q1_active_host
+ * N_1 = (nx+1)(ny+1) bytes, with the definitions above (any output may be NULL).
+ * The same routine sets the roles of every eth_mgrid level. */
+eth_status eth_mask_roles(int nx, int ny, const unsigned char* active_host, int outflow, unsigned char* fixed_host,
+                          unsigned char* dirichlet_host, unsigned char* q1_active_host);
 /* N_v, N_1, N_0 and N_t = 2 N_v + N_1 + N_0 (any pointer may be NULL). */
 eth_status eth_mgrid_sizes(const eth_mgrid* g, long long* nv, long long* n1, long long* n0, long long* nt);
 /* Host copies of the node roles (N_v bytes: 1 on fixed = Dirichlet or inactive

@@ -1970,6 +1970,21 @@ void eth_mgrid_destroy(eth_mgrid* g) {
   mgrid_free(g);
 }
 
+eth_status eth_mask_roles(int nx, int ny, const unsigned char* active_host, int outflow, unsigned char* fixed_host,
+                          unsigned char* dirichlet_host, unsigned char* q1_active_host) {
+  if (!active_host || nx < 1 || ny < 1 || (outflow != 0 && outflow != 1)) {
+    set_error("eth_mask_roles: need nx, ny >= 1, an element mask and outflow in {0, 1}");
+    return ETH_EINVAL;
+  }
+  std::vector<unsigned char> act((size_t)nx * ny), fix, dir, q1a;
+  for (size_t e = 0; e < act.size(); ++e) act[e] = active_host[e] ? 1 : 0;
+  node_roles(nx, ny, outflow, act, fix, dir, q1a);
+  if (fixed_host) std::memcpy(fixed_host, fix.data(), fix.size());
+  if (dirichlet_host) std::memcpy(dirichlet_host, dir.data(), dir.size());
+  if (q1_active_host) std::memcpy(q1_active_host, q1a.data(), q1a.size());
+  return ETH_OK;
+}
+
 eth_status eth_mgrid_sizes(const eth_mgrid* g, long long* nv, long long* n1, long long* n0, long long* nt) {
   if (!g) { set_error("eth_mgrid_sizes: NULL grid"); return ETH_EINVAL; }
   if (nv) *nv = (long long)g->nv;

@@ -92,6 +92,7 @@ def load(path=LIB_PATH):
         "eth_apply_k_dot_static": (i, [i, d, d, d, d, d, i, vp, vp, vp, vp]),
         "eth_apply_pcd": (i, [vp, i, i, i, i, vp, vp]),
         "eth_apply_mqcheb": (i, [vp, i, i, d, d, vp, vp]),
+        "eth_mask_roles": (i, [i, i, vp, i, vp, vp, vp]),
         "eth_mgrid_create": (i, [i, i, d, d, d, vp, i, vp, ctypes.POINTER(vp)]),
         "eth_mgrid_destroy": (None, [vp]),
         "eth_mgrid_sizes": (i, [vp, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(ctypes.c_longlong),
@@ -389,6 +390,17 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def mask_roles(nx, ny, active, outflow=True):
+    """Host-side node roles of a masked grid: (fixed, dirichlet) over the Q2 lattice and the
+    active Q1 nodes, as boolean numpy arrays (no device needed)."""
+    act = np.ascontiguousarray(np.asarray(active, dtype=bool).reshape(int(ny), int(nx)).astype(np.uint8))
+    nv, n1 = (2 * nx + 1) * (2 * ny + 1), (nx + 1) * (ny + 1)
+    fx = np.zeros(nv, dtype=np.uint8); dr = np.zeros(nv, dtype=np.uint8); qa = np.zeros(n1, dtype=np.uint8)
+    c = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(load().eth_mask_roles(int(nx), int(ny), c(act), int(bool(outflow)), c(fx), c(dr), c(qa)))
+    return fx.astype(bool), dr.astype(bool), qa.astype(bool)
 
 
 class MGrid:
