@@ -1163,6 +1163,19 @@ static eth_status q2_jr(eth_grid* g, Level<T>& L, const TI* b, T* bcopy, T omega
   return ETH_OK;
 }
 
+// the first sweep of a coarser level whose right-hand side is the restriction of
+// the finer level's residual rf, formed on the fly (b written to L.b)
+template <class T, int CF>
+static eth_status q2_rjr(eth_grid* g, Level<T>& L, const T* rf, T omega, const int* done) {
+  Q2Params<T, T, T> P{};
+  P.n = L.n; P.hx = (T)L.hx; P.hy = (T)L.hy; P.nu = (T)L.nu; P.sd = (T)L.sd;
+  P.w = L.w; P.dinv = L.dinv; P.omega = omega; P.done = done;
+  P.bx = rf; P.y = L.r; P.y2 = L.x; P.bcopy = L.b;
+  ETH_CUDA((launch_q2<T, T, T, QF_DIFF | QF_XIN | QF_UOUT | QF_SRC_JB | QF_SRC_RJB | CF, EPI_JR>(P, g->s)));
+  g->launches++;
+  return ETH_OK;
+}
+
 template <class T, class TO, int CF>
 static eth_status q2_ps(eth_grid* g, Level<T>& L, const T* x, const T* xc, TO* y, T omega, const TO* bsrc,
                         const int* done, const Slot* slot, int slot_off, const TO* dv) {
@@ -1212,16 +1225,20 @@ static eth_status vcycle_vel_fused_cf(eth_grid* g, Hier<T>& H, const double* v, 
                                       const int* done, const Slot* slot, int slot_off, int Lc) {
   const T om = (T)H.omega;
   std::vector<T*> res(H.lv.size(), nullptr);
+  // level 0 from v; each coarser multi-CTA level restricts the finer level's residual
+  // inside its first sweep (no separate restriction launch); the coarse V-cycle
+  // kernel's level gets an explicit restriction
   for (int l = 0; l < Lc; ++l) {
     Level<T>& L = H.lv[l];
     const size_t N = 2 * (size_t)L.n + 1, nv = N * N;
     if (l == 0) ETH_TRY((q2_jr<T, double, CF>(g, L, v, L.b, om, done)));
-    else ETH_TRY((q2_jr<T, T, CF>(g, L, L.b, nullptr, om, done)));
+    else ETH_TRY((q2_rjr<T, CF>(g, L, H.lv[l - 1].r, om, done)));
     for (int s = 1; s < pre; ++s) {
       ETH_TRY((q2_level<T, T, EPI_SMOOTH, CF>(g, L, L.x, L.t, om, nullptr, done, nullptr, 0, nullptr)));
       ETH_CUDA(cudaMemcpyAsync(L.x, L.t, 2 * nv * sizeof(T), cudaMemcpyDeviceToDevice, g->s));
       ETH_TRY((q2_level<T, T, EPI_RESID, CF>(g, L, L.x, L.r, om, nullptr, done, nullptr, 0, nullptr)));
     }
+    if (l + 1 < Lc) continue;
     const Level<T>& Cn = H.lv[l + 1];
     const size_t Nc = 2 * (size_t)Cn.n + 1;
     k_q2_restrict<T><<<gsize(Nc * Nc), 256, 0, g->s>>>(Cn.n, L.r, Cn.b, done);

@@ -45,9 +45,13 @@ enum : int {
   QF_SD = 2048,     // streamline diffusion sum_T d_T int (w.grad u)(w.grad v) (coarse levels)
   QF_SRC_JB = 4096, // x field = omega * dinv * b (first Jacobi sweep from zero), b read from bx
   QF_SRC_XPC = 8192,// x field = x + P xc (coarse-grid correction prolongated on the fly)
+  QF_SRC_RJB = 16384,// with QF_SRC_JB: b = P^T r_f, the finer level's residual bx restricted on the fly
 };
 enum : int { EPI_APPLY = 0, EPI_SMOOTH = 1, EPI_RESID = 2, EPI_SCALE = 3, EPI_BSUB = 4, EPI_JR = 5 };
 // EPI_JR (with QF_SRC_JB): y = b - F x and y2 = x = omega D^{-1} b; bcopy = b (optional).
+// With QF_SRC_RJB, b is the restriction of the finer level's residual (bx, lattice
+// 4n+1), gathered per staged node with the weights and in the order of the
+// stand-alone restriction kernel, and bcopy receives it (required).
 // EPI_SCALE: y = dinv * (op x) on the interior, 0 on the boundary.
 // EPI_BSUB:  y = bsrc - (op x) on the interior, bsrc on the boundary.
 
@@ -124,6 +128,42 @@ __device__ __forceinline__ TO cvt_out(CT v) {
 #else
   return cvt<TO, CT>(v);
 #endif
+}
+
+// 1D Q2 restriction weight of the fine node at offset o in [-3, 3] from 2I (coarse
+// node I odd: an element midpoint; even: an element vertex).
+__device__ __forceinline__ float rjb_w(int odd, int o) {
+  if (o == 0) return 1.f;
+  if (odd) return (o == -1 || o == 1) ? 0.75f : 0.f;
+  return (o == -1 || o == 1) ? 0.375f : ((o == -3 || o == 3) ? -0.125f : 0.f);
+}
+
+// b at coarse node (i, j) (interior) = P^T r_f: fine lattice Nf = 2N - 1.
+template <class CT, class TI>
+__device__ __forceinline__ void rjb_gather(const TI* __restrict__ rf, int N, int i, int j, CT& b0, CT& b1) {
+  const int Nf = 2 * N - 1;
+  const int nvf = Nf * Nf;
+  const int ox = i & 1, oy = j & 1;
+  CT s0 = 0, s1 = 0;
+#pragma unroll
+  for (int u = -3; u <= 3; ++u) {
+    const float wyv = rjb_w(oy, u);
+    if (wyv == 0.f) continue;
+    const int row = (2 * j + u) * Nf;
+    CT t0 = 0, t1 = 0;
+#pragma unroll
+    for (int v = -3; v <= 3; ++v) {
+      const float wxv = rjb_w(ox, v);
+      if (wxv == 0.f) continue;
+      const int f = row + 2 * i + v;
+      t0 += (CT)wxv * (CT)rf[f];
+      t1 += (CT)wxv * (CT)rf[f + nvf];
+    }
+    s0 += (CT)wyv * t0;
+    s1 += (CT)wyv * t1;
+  }
+  b0 = s0;
+  b1 = s1;
 }
 
 template <class CT, int F>
@@ -321,7 +361,7 @@ __global__ void __launch_bounds__(TEX * TY, q2_min_blocks<CT, F, EPI, TY>())
   constexpr int TEY = TY, OEY = TY - 1, Q2T = TEX * TY, SQY = 2 * TY + 1, SPY = TY + 1;
   constexpr bool CONV = F & QF_CONV, XIN = F & QF_XIN, PIN = F & QF_PIN, HP0 = F & QF_P0,
                  UOUT = F & QF_UOUT, POUT = F & QF_POUT, DOT = F & QF_DOT, NOBC = F & QF_NOBC,
-                 JB = F & QF_SRC_JB, XPC = F & QF_SRC_XPC;
+                 JB = F & QF_SRC_JB, XPC = F & QF_SRC_XPC, RJB = (F & QF_SRC_RJB) && (F & QF_SRC_JB);
   if (P.done != nullptr && *P.done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sx = reinterpret_cast<CT*>(smem_raw);                 // [2][SQY][SQX]
@@ -329,6 +369,7 @@ __global__ void __launch_bounds__(TEX * TY, q2_min_blocks<CT, F, EPI, TY>())
   CT* sp1 = sw + (CONV ? 2 * SQY * SQX : 0);                // [SPY][SPX]
   CT* sp0 = sp1 + SPY * SPX;                                // [TEY][TEX]
   CT* eo = sp0 + TEY * TEX;                                 // [NEO][Q2T]
+  CT* sb = eo + NEO * Q2T;                                  // [2][SQY][SQX] (RJB: the restricted b)
 
   const int n = P.n, N = 2 * n + 1;
   const int nv = N * N;   // 32-bit offsets: 2 N_v + N_1 + N_0 < 2^31 for n <= 8192
@@ -355,10 +396,24 @@ __global__ void __launch_bounds__(TEX * TY, q2_min_blocks<CT, F, EPI, TY>())
         const bool bnd = !NOBC && (i == 0 || j == 0 || i == N - 1 || j == N - 1);
         if (XIN && !bnd) {
           ok[r] = true;
-          if (JB) { v0[r] = P.bx[g]; v1[r] = P.bx[g + nv]; w0[r] = P.dinv[g]; }
+          if (RJB) { w0[r] = P.dinv[g]; }
+          else if (JB) { v0[r] = P.bx[g]; v1[r] = P.bx[g + nv]; w0[r] = P.dinv[g]; }
           else { v0[r] = P.x[g]; v1[r] = P.x[g + nv]; }
         }
         if (CONV) { if (JB) w1[r] = P.w[g]; else { w0[r] = P.w[g]; w1[r] = P.w[g + nv]; } }
+      }
+    }
+    if (RJB) {   // b = P^T r_f at the staged interior nodes, kept in sb for the epilogue
+#pragma unroll 1
+      for (int r = 0; r < NLD; ++r) {
+        const int k = tid + r * Q2T;
+        CT b0 = 0, b1 = 0;
+        if (ok[r]) {
+          const int lj = k / SQX, li = k - lj * SQX;
+          rjb_gather<CT, TI>(P.bx, N, gi0 + li, gj0 + lj, b0, b1);
+        }
+        if (k < SQY * SQX) { sb[k] = b0; sb[SQY * SQX + k] = b1; }
+        v0[r] = (TI)b0; v1[r] = (TI)b1;
       }
     }
 #pragma unroll
@@ -540,7 +595,7 @@ __global__ void __launch_bounds__(TEX * TY, q2_min_blocks<CT, F, EPI, TY>())
           P.y2[g] = 0; P.y2[g + nv] = 0;
           if (P.bcopy) { P.bcopy[g] = 0; P.bcopy[g + nv] = 0; }
         } else {
-          const CT b0 = cvt<CT, TI>(P.bx[g]), b1 = cvt<CT, TI>(P.bx[g + nv]);
+          const CT b0 = RJB ? sb[sI] : cvt<CT, TI>(P.bx[g]), b1 = RJB ? sb[SQY * SQX + sI] : cvt<CT, TI>(P.bx[g + nv]);
           o0 = (TO)(b0 - s0); o1 = (TO)(b1 - s1);
           P.y2[g] = sx[sI]; P.y2[g + nv] = sx[SQY * SQX + sI];
           if (P.bcopy) { P.bcopy[g] = b0; P.bcopy[g + nv] = b1; }
@@ -600,6 +655,7 @@ inline size_t q2_smem_bytes(int F, size_t ct_size, int ty = ETH_TEY) {
   const bool conv = F & QF_CONV;
   const size_t sqy = 2 * ty + 1, spy = ty + 1, q2t = (size_t)TEX * ty;
   size_t nct = 2 * sqy * SQX + (conv ? 2 * sqy * SQX : 0) + spy * SPX + q2t + NEO * q2t;
+  if ((F & QF_SRC_RJB) && (F & QF_SRC_JB)) nct += 2 * sqy * SQX;
   return nct * ct_size;
 }
 
