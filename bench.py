@@ -585,14 +585,16 @@ def profile_apply(n, kind, rows):
 
 def profile_solve(n, kind):
     """Two default solves of the n x n workload (Stokes MMS or Oseen cavity, nu = 1/100)
-    for an ncu launch list of the solver (the second solve is the one to read)."""
+    for an ncu launch list of the solver (the second solve is the one to read).  The
+    Stokes solves replay their MINRES graph from the host (graph = 2): the same kernels as
+    the device-side loop, whose conditional-node body ncu does not list launch by launch."""
     import __graft_entry__ as ge
     ge.build()
     from paper_2303_10233_gb300 import eth, workloads as W
     w = W.oseen_cavity(n, nu=0.01, seed=1) if kind == "oseen" else W.mms(n, seed=SEED)
     G = eth.problem(w)
     for _ in range(2):
-        _, _, st = G.solve(tol=TOL)
+        _, _, st = G.solve(tol=TOL, graph=2 if kind == "stokes" else 1)
     print(f"profile_solve n={n} kind={kind} its={st['iters_stage1']}+{st['iters_stage2']} "
           f"ms={st['seconds'] * 1e3:.1f} launches={st['kernel_launches']}")
     G.close()
