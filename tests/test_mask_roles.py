@@ -51,3 +51,4 @@ def test_bad_arguments_rejected():
     assert L.eth_mask_roles(0, 2, act.ctypes.data_as(ctypes.c_void_p), 1, None, None, None) == 1
     assert L.eth_mask_roles(2, 2, act.ctypes.data_as(ctypes.c_void_p), 2, None, None, None) == 1
     assert L.eth_mask_roles(2, 2, None, 1, None, None, None) == 1
+
