@@ -52,3 +52,26 @@ def test_bad_arguments_rejected():
     assert L.eth_mask_roles(2, 2, act.ctypes.data_as(ctypes.c_void_p), 2, None, None, None) == 1
     assert L.eth_mask_roles(2, 2, None, 1, None, None, None) == 1
 
+
+
+def test_masked_grid_arguments_rejected_on_the_host():
+    """eth_mgrid_create and the masked-grid calls reject bad arguments before any device
+    work (the checks run on machines without a GPU)."""
+    import ctypes
+    from paper_2303_10233_gb300 import eth
+    L = eth.load()
+    act = np.ones(12, dtype=np.uint8)
+    none = np.zeros(12, dtype=np.uint8)
+    h = ctypes.c_void_p()
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    assert L.eth_mgrid_create(0, 2, 0.5, 0.0, 0.0, p(act), 1, None, ctypes.byref(h)) == 1
+    assert L.eth_mgrid_create(6, 2, -1.0, 0.0, 0.0, p(act), 1, None, ctypes.byref(h)) == 1
+    assert L.eth_mgrid_create(6, 2, 0.5, 0.0, 0.0, p(act), 2, None, ctypes.byref(h)) == 1
+    assert L.eth_mgrid_create(6, 2, 0.5, 0.0, 0.0, p(none), 1, None, ctypes.byref(h)) == 1
+    assert L.eth_mgrid_create(6, 2, 0.5, 0.0, 0.0, None, 1, None, ctypes.byref(h)) == 1
+    assert L.eth_mgrid_create(6, 2, 0.5, 0.0, 0.0, p(act), 1, None, None) == 1
+    assert b"active" in L.eth_last_error() or b"NULL" in L.eth_last_error()
+    assert L.eth_mgrid_apply(None, 0, None, None) == 1
+    assert L.eth_mgrid_solve(None, None, None, None, None) == 1
+    assert L.eth_mgrid_picard(None, None, None, 5, None, None, None, None) == 1
+    assert L.eth_mgrid_sizes(None, None, None, None, None) == 1
