@@ -389,8 +389,14 @@ eth_status eth_mgrid_rhs(eth_mgrid* g, const double* ubc_dev, double* b_dev);
  * B1^T), to ||r|| <= c_stage tol ||b_red||; Step II GMRES on K with M_1 =
  * [F B^T; 0 -(1/nu) M_Q]^{-1} to tol ||b||.  F^{-1} is one V-cycle of the
  * masked multigrid (FP32 levels, damped Jacobi, streamline diffusion on the
- * levels of an Oseen operator), Ap^{-1} and M_Q^+ inner Jacobi PCG, Q1^{-1} ten
- * Chebyshev steps.  On exit k^T p = 0.  stats: stage iterations, the FP64 true
+ * levels of an Oseen operator); Ap^{-1} is three CG steps preconditioned by a
+ * V-cycle of the Q1 Laplacian with a unit shift on the outflow column; M_Q^+
+ * eliminates the P0 block and takes three CG steps on its Schur complement,
+ * preconditioned by a natural-boundary Q1 V-cycle, with k projected out;
+ * Q1^{-1} is ten Chebyshev steps.  Without a wind (the Stokes problem) Step I
+ * uses the Stokes limit M_S^{-1} = nu Q1^{-1}.  With opts->graph != 0 the
+ * preconditioner and operator of each Arnoldi step replay from a CUDA graph on
+ * the handle's internal stream.  On exit k^T p = 0.  stats: stage iterations, the FP64 true
  * relative residual, the Prop. 2 quantities (||z*||^2 and its bound), status
  * ETH_ENOTCONV when tol was not reached within opts->maxit.  Synchronises. */
 eth_status eth_mgrid_solve(eth_mgrid* g, const eth_opts* opts, const double* b_dev, double* x_dev, eth_stats* stats);
