@@ -23,8 +23,9 @@
 // carrying the inflow Robin term; Step II on the full system with M_1) by
 // restarted flexible GMRES, velocity blocks by one FP32 V-cycle of a masked
 // geometric multigrid hierarchy (halving nx and ny while the mask stays
-// 2 x 2-nested), dense exact solve on the coarsest level; Picard iteration
-// around it.
+// 2 x 2-nested), dense exact solve on the coarsest level; the pressure solves
+// (Ap^{-1}, the Schur complement of M_Q) by a few CG steps preconditioned by
+// masked Q1 V-cycles; Picard iteration around it.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
